@@ -1,0 +1,266 @@
+/*
+ * gbrt.h -- C ABI of the GB300 molecular ambient-occlusion ray tracer.
+ *
+ * The library renders molecular scenes of spheres (atoms) and open cylinders
+ * (bonds) the way the paper's Tachyon runs do (Sec. 2: "-res W H -trans_vmd
+ * -rescale_lights 0.3 -add_skylight 1.0"): one primary ray per pixel, its
+ * nearest hit, Monte-Carlo ambient-occlusion shadow rays from the hit point,
+ * then Phong shading under rescaled directional lights plus an AO-weighted
+ * skylight. Rays walk a uniform grid built on the device (Table 5's
+ * "Preprocess" phase). Every step runs in CUDA kernels compiled for sm_103a.
+ *
+ * Conventions for every entry point:
+ *  - Return value: GBRT_OK (0) or a negative GBRT_E* code; nothing throws.
+ *    gbrt_strerror() names a code. Invalid arguments are rejected with
+ *    GBRT_EINVAL before any work is enqueued.
+ *  - Pointers are device pointers unless the call's flags say
+ *    GBRT_HOST_PTRS. Device pointers must be valid on the context's device.
+ *  - Calls enqueue work on the context's stream (the caller's stream, e.g.
+ *    the current PyTorch stream) and return without waiting, except where a
+ *    call says it synchronises. Output buffers are owned by the caller and
+ *    must stay alive until the stream reaches the work.
+ *  - Scenes and grids are owned by the library until gbrt_scene_free /
+ *    gbrt_grid_free. A context is used by one host thread at a time.
+ *  - Kernel-side failures (a grid walk that exceeds its step bound, a work
+ *    queue wait that runs out) set a device error word; gbrt_sync() reports
+ *    it (GBRT_ETRAVERSAL / GBRT_ETIMEDOUT) and clears it.
+ */
+#ifndef GBRT_H
+#define GBRT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define GBRT_API __attribute__((visibility("default")))
+#else
+#define GBRT_API
+#endif
+
+#define GBRT_VERSION 1
+
+/* ---- error codes ---- */
+#define GBRT_OK 0
+#define GBRT_EINVAL (-1)      /* invalid argument or scene data */
+#define GBRT_ENOMEM (-2)      /* device or pinned allocation failed */
+#define GBRT_EDEVICE (-3)     /* CUDA runtime error / no device */
+#define GBRT_ETIMEDOUT (-4)   /* a bounded device wait ran out */
+#define GBRT_ETRAVERSAL (-5)  /* a grid walk exceeded its step bound */
+
+/* ---- flags ---- */
+#define GBRT_DEVICE_PTRS 0
+#define GBRT_HOST_PTRS 1      /* array arguments are host memory */
+#define GBRT_BATCH_GRAPH 2    /* gbrt_render_batch: replay through a CUDA graph */
+
+/* ---- precision ---- */
+#define GBRT_FP32 0  /* FP32 traversal, intersection and shading; FP64 root + re-projection */
+#define GBRT_FP64 1  /* FP64 throughout (the paper's "double precision", Sec. 2) */
+
+#define GBRT_CAMERA_ORTHO 0
+#define GBRT_CAMERA_PINHOLE 1
+#define GBRT_MAX_LIGHTS 8
+#define GBRT_MISS 0xFFFFFFFFu    /* hit id of a pixel whose ray hits nothing */
+#define GBRT_MAX_SAMPLES 4096    /* ao_samples bound */
+#define GBRT_MAX_DIM 65536       /* width/height bound; width*height < 2^31 */
+
+typedef struct gbrt_ctx gbrt_ctx;
+typedef struct gbrt_scene gbrt_scene;
+typedef struct gbrt_grid gbrt_grid;
+
+/* Camera. Pixel (i, j) -- column i, row j, row 0 at the top -- uses
+ *   u = half_w (2 (i + 0.5)/W - 1),  v = half_h (1 - 2 (j + 0.5)/H).
+ * Ortho: ray origin eye + u right + v up, direction dir.
+ * Pinhole: origin eye, direction normalize(dir + u right + v up).
+ * dir, up, right: unit and mutually orthogonal. */
+typedef struct gbrt_camera {
+    int32_t kind;
+    int32_t reserved;
+    double eye[3];
+    double dir[3];
+    double up[3];
+    double right[3];
+    double half_w;
+    double half_h;
+} gbrt_camera;
+
+/* Directional lights: dir[l] is the unit vector toward light l. Every light's
+ * intensity is multiplied by `scale` (tachyon -rescale_lights, Sec. 2); the
+ * skylight (tachyon -add_skylight, Sec. 2) weights the AO term. */
+typedef struct gbrt_lights {
+    int32_t n;
+    int32_t reserved;
+    double dir[GBRT_MAX_LIGHTS][3];
+    double intensity[GBRT_MAX_LIGHTS];
+    double scale;
+    double skylight;
+} gbrt_lights;
+
+/* Per-frame parameters.
+ *  precision   GBRT_FP32 | GBRT_FP64
+ *  seed, frame Philox4x32-10 key = (seed low word, seed high word); the AO
+ *              sample s of pixel q uses counter (q, s, frame, 0xA0) and the
+ *              24-bit fractions of output words 0 and 1
+ *  eps         AO rays start at the re-projected hit point + eps * normal
+ *  ao_maxdist  AO rays count hits with 0 < t <= ao_maxdist (may be +inf)
+ *  k_ao, k_d, k_s, phong_exp  material: colour =
+ *      clamp01(albedo (skylight k_ao V + sum_l scale I_l k_d max(0, n.l))
+ *              + sum_{l: n.l > 0} scale I_l k_s max(0, r_l.v)^phong_exp)
+ *      with V the fraction of AO samples that escape (V = 1 when
+ *      ao_samples = 0), r_l the mirror of l about n, v = -ray direction
+ *  background  colour of pixels whose primary ray hits nothing
+ *  out_flags   GBRT_HOST_PTRS: the render's output pointers are host memory
+ *              (the call then synchronises). */
+typedef struct gbrt_params {
+    int32_t precision;
+    int32_t out_flags;
+    uint64_t seed;
+    uint32_t frame;
+    uint32_t reserved;
+    double eps;
+    double ao_maxdist;
+    double k_ao;
+    double k_d;
+    double k_s;
+    double phong_exp;
+    double background[3];
+} gbrt_params;
+
+/* One frame of a batch (gbrt_render_batch). Fields as for gbrt_render. */
+typedef struct gbrt_render_item {
+    const gbrt_scene* scene;
+    const gbrt_grid* grid;
+    gbrt_camera camera;
+    int32_t width;
+    int32_t height;
+    int32_t ao_samples;
+    int32_t reserved;
+    gbrt_lights lights;
+    gbrt_params params;
+    void* out_rgb;
+    uint32_t* out_hit_ids;
+    uint32_t* out_ao_visible;
+} gbrt_render_item;
+
+/* Launch shape of the render kernels, chosen by the autotuner.
+ *  tile_w x tile_h  pixels of one work item (tile_w * tile_h a multiple of 32)
+ *  block            threads per CTA (multiple of 32, <= 1024)
+ *  ctas_per_sm      resident CTAs per SM of the persistent launch (0 = max)
+ *  lanes_refill     replace a finished pixel's lane as soon as it finishes
+ *                   (1) or only when the whole warp is done (0) */
+typedef struct gbrt_tuning {
+    int32_t tile_w;
+    int32_t tile_h;
+    int32_t block;
+    int32_t ctas_per_sm;
+    int32_t lanes_refill;
+    int32_t reserved[3];
+} gbrt_tuning;
+
+/* Library version (GBRT_VERSION). Host only; needs no device. */
+GBRT_API int gbrt_version(void);
+
+/* Static string naming an error code. Host only; needs no device. */
+GBRT_API const char* gbrt_strerror(int code);
+
+/* Create a context on CUDA device `device` that enqueues on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream; owned by the caller).
+ * Allocates the context's device error word. GBRT_EDEVICE without a device. */
+GBRT_API int gbrt_create(gbrt_ctx** out, int device, void* cuda_stream);
+
+/* Change the stream later calls enqueue on. */
+GBRT_API int gbrt_set_stream(gbrt_ctx* ctx, void* cuda_stream);
+
+/* Wait for the context's stream, then read and clear the device error word. */
+GBRT_API int gbrt_sync(gbrt_ctx* ctx);
+
+/* Destroy a context (synchronises its stream first). Scenes and grids must be
+ * freed before. NULL is accepted. */
+GBRT_API int gbrt_destroy(gbrt_ctx* ctx);
+
+/* Upload a scene (Sec. 2: the molecular model of spheres and cylinders).
+ *  spheres    float32 [S][4]  centre x y z, radius > 0
+ *  cylinders  float32 [C][7]  end p0 x y z, end p1 x y z, radius > 0, p0 != p1
+ *             (open tubes: no end caps)
+ *  color_idx  uint32 [S + C]  palette entry of each object, < K; objects are
+ *             numbered spheres 0..S-1 then cylinders S..S+C-1 (global ids)
+ *  palette    float32 [K][3]  linear RGB albedo
+ *  flags      GBRT_HOST_PTRS if the four arrays are host memory
+ * The library copies the data into its own device layout (float4 sphere and
+ * cylinder records, FP64 copies for the hit refinement) and computes the scene
+ * box. S or C may be 0 (an empty scene renders background). Synchronises.
+ * GBRT_EINVAL on non-finite values, radius <= 0, zero-length cylinders or a
+ * colour index >= K. */
+GBRT_API int gbrt_scene_upload(gbrt_ctx* ctx, const float* spheres, int64_t n_spheres, const float* cylinders,
+                               int64_t n_cylinders, const uint32_t* color_idx, const float* palette,
+                               int32_t n_palette, int flags, gbrt_scene** out);
+
+/* Scene size in bytes on the device, and object counts (host only). */
+GBRT_API int gbrt_scene_info(const gbrt_scene* scene, int64_t* n_spheres, int64_t* n_cylinders,
+                             int64_t* device_bytes);
+
+GBRT_API int gbrt_scene_free(gbrt_ctx* ctx, gbrt_scene* scene);
+
+/* Build the uniform grid (Table 5 "Preprocess"): about lambda * (S + C) cells
+ * over the scene box (lambda <= 0 selects 2.0); each object is listed in every
+ * cell its padded bounding box overlaps, ids ascending within a cell
+ * (counting sort: count, exclusive scan, scatter, per-cell sort). Synchronises
+ * (the reference count sizes the item array). */
+GBRT_API int gbrt_grid_build(gbrt_ctx* ctx, const gbrt_scene* scene, float lambda, gbrt_grid** out);
+
+/* Grid geometry (host only): cells per axis, padded box, total references. */
+GBRT_API int gbrt_grid_info(const gbrt_grid* grid, int32_t dims[3], float lo[3], float hi[3], int64_t* refs,
+                            int64_t* device_bytes);
+
+GBRT_API int gbrt_grid_free(gbrt_ctx* ctx, gbrt_grid* grid);
+
+/* Render one frame (Sec. 2's tachyon run: -res width height, AO with
+ * ao_samples Monte-Carlo samples per pixel, lights, skylight).
+ *  out_rgb         [height][width][3], float32 for GBRT_FP32, float64 for GBRT_FP64
+ *  out_hit_ids     optional uint32 [height][width]: nearest object id, GBRT_MISS
+ *  out_ao_visible  optional uint32 [height][width]: AO samples that escaped
+ * Output pointers are device memory unless params->out_flags has
+ * GBRT_HOST_PTRS, in which case the library renders into its own device
+ * buffer, copies back and synchronises. Asynchronous otherwise. */
+GBRT_API int gbrt_render(gbrt_ctx* ctx, const gbrt_scene* scene, const gbrt_grid* grid, const gbrt_camera* camera,
+                         int32_t width, int32_t height, int32_t ao_samples, const gbrt_lights* lights,
+                         const gbrt_params* params, void* out_rgb, uint32_t* out_hit_ids,
+                         uint32_t* out_ao_visible);
+
+/* Render n frames of uneven size through one persistent launch that drains a
+ * device queue of (frame, tile) work items. Each item is rendered exactly as
+ * gbrt_render would render it alone. Items' output pointers are device memory.
+ * flags: GBRT_BATCH_GRAPH replays the upload + launch through a CUDA graph
+ * captured on first use for this batch size. Asynchronous. */
+GBRT_API int gbrt_render_batch(gbrt_ctx* ctx, const gbrt_render_item* items, int32_t n, int flags);
+
+/* AO visibility of explicit points (Sec. 2's Monte-Carlo sampling of
+ * illumination, as a probe): for point k, `ao_samples` cosine-weighted rays
+ * from pts[k] + eps * nrm[k] with Philox counter (k, s, frame, 0xA0);
+ * out_visibility[k] = escaped / ao_samples. pts, nrm: float64 [n][3] device,
+ * nrm unit. Uses params precision, seed, frame, eps and ao_maxdist. Async. */
+GBRT_API int gbrt_ao_probe(gbrt_ctx* ctx, const gbrt_scene* scene, const gbrt_grid* grid, const double* pts,
+                           const double* nrm, int64_t n, int32_t ao_samples, const gbrt_params* params,
+                           float* out_visibility);
+
+/* Raw Philox4x32-10 blocks (the AO sampler's generator): out[k] =
+ * Philox(counter ctr[k] (4 words), key key[k] (2 words)). Device arrays,
+ * uint32 [n][4], [n][2], [n][4]. Async. */
+GBRT_API int gbrt_philox4x32_10(gbrt_ctx* ctx, const uint32_t* ctr, const uint32_t* key, int64_t n,
+                                uint32_t* out);
+
+/* Kernel launch shape used by later renders (see gbrt_tuning). */
+GBRT_API int gbrt_set_tuning(gbrt_ctx* ctx, const gbrt_tuning* tuning);
+GBRT_API int gbrt_get_tuning(const gbrt_ctx* ctx, gbrt_tuning* tuning);
+
+/* Number of kernels this context has launched so far (host counter). */
+GBRT_API int64_t gbrt_launch_count(const gbrt_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBRT_H */

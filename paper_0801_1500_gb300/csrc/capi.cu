@@ -1,0 +1,414 @@
+// The C ABI (include/gbrt.h): argument validation, handles, streams, error
+// word, and the frame descriptors handed to the kernels. No C++ exception
+// crosses this boundary.
+#include <math.h>
+#include <string.h>
+
+#include <cmath>
+#include <new>
+
+#include "gbrt_internal.h"
+
+using namespace gbrt;
+
+namespace {
+
+// Makes the context's device current for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+bool finite3(const double* v) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
+
+int check_frame_args(const gbrt_scene* scene, const gbrt_grid* grid, const gbrt_camera* cam, int32_t W, int32_t H,
+                     int32_t spp, const gbrt_lights* lights, const gbrt_params* params, const void* out_rgb) {
+    if (!scene || !grid || !cam || !lights || !params || !out_rgb) return GBRT_EINVAL;
+    if (W <= 0 || H <= 0 || W > GBRT_MAX_DIM || H > GBRT_MAX_DIM || (int64_t)W * H >= (1ll << 31)) return GBRT_EINVAL;
+    if (spp < 0 || spp > GBRT_MAX_SAMPLES) return GBRT_EINVAL;
+    if (cam->kind != GBRT_CAMERA_ORTHO && cam->kind != GBRT_CAMERA_PINHOLE) return GBRT_EINVAL;
+    if (!finite3(cam->eye) || !finite3(cam->dir) || !finite3(cam->up) || !finite3(cam->right)) return GBRT_EINVAL;
+    if (!(cam->half_w > 0) || !(cam->half_h > 0) || !std::isfinite(cam->half_w) || !std::isfinite(cam->half_h))
+        return GBRT_EINVAL;
+    double dl = cam->dir[0] * cam->dir[0] + cam->dir[1] * cam->dir[1] + cam->dir[2] * cam->dir[2];
+    if (!(dl > 0)) return GBRT_EINVAL;
+    if (lights->n < 0 || lights->n > GBRT_MAX_LIGHTS) return GBRT_EINVAL;
+    for (int l = 0; l < lights->n; ++l)
+        if (!finite3(lights->dir[l]) || !std::isfinite(lights->intensity[l])) return GBRT_EINVAL;
+    if (!std::isfinite(lights->scale) || !std::isfinite(lights->skylight)) return GBRT_EINVAL;
+    if (params->precision != GBRT_FP32 && params->precision != GBRT_FP64) return GBRT_EINVAL;
+    if (!(params->eps >= 0) || !std::isfinite(params->eps)) return GBRT_EINVAL;
+    if (!(params->ao_maxdist > 0)) return GBRT_EINVAL;  // +inf allowed
+    if (!std::isfinite(params->k_ao) || !std::isfinite(params->k_d) || !std::isfinite(params->k_s) ||
+        !std::isfinite(params->phong_exp) || !finite3(params->background))
+        return GBRT_EINVAL;
+    if (grid->dev.cells == nullptr) return GBRT_EINVAL;
+    return GBRT_OK;
+}
+
+FrameDev make_frame(const gbrt_scene* scene, const gbrt_grid* grid, const gbrt_camera* cam, int32_t W, int32_t H,
+                    int32_t spp, const gbrt_lights* lights, const gbrt_params* p, void* out_rgb, uint32_t* out_ids,
+                    uint32_t* out_vis) {
+    FrameDev f;
+    memset(&f, 0, sizeof(f));
+    f.scene = scene->view();
+    f.grid = grid->dev;
+    for (int k = 0; k < 3; ++k) {
+        f.eye[k] = cam->eye[k];
+        f.dir[k] = cam->dir[k];
+        f.up[k] = cam->up[k];
+        f.right[k] = cam->right[k];
+    }
+    f.half_w = cam->half_w;
+    f.half_h = cam->half_h;
+    f.cam_kind = cam->kind;
+    f.W = W;
+    f.H = H;
+    f.spp = spp;
+    f.frame = p->frame;
+    f.seed_lo = (uint32_t)(p->seed & 0xFFFFFFFFull);
+    f.seed_hi = (uint32_t)(p->seed >> 32);
+    f.precision = p->precision;
+    f.nl = lights->n;
+    for (int l = 0; l < lights->n; ++l) {
+        for (int k = 0; k < 3; ++k) {
+            f.ldir[l][k] = lights->dir[l][k];
+            f.ldir_f[l][k] = (float)lights->dir[l][k];
+        }
+        f.lI[l] = lights->intensity[l] * lights->scale;
+        f.lI_f[l] = (float)f.lI[l];
+    }
+    f.sky_kao = lights->skylight * p->k_ao;
+    f.k_d = p->k_d;
+    f.k_s = p->k_s;
+    f.phong = p->phong_exp;
+    f.sky_kao_f = (float)f.sky_kao;
+    f.k_d_f = (float)f.k_d;
+    f.k_s_f = (float)f.k_s;
+    f.phong_f = (float)f.phong;
+    f.eps = p->eps;
+    f.ao_maxdist = p->ao_maxdist;
+    f.ao_maxdist_f = (float)p->ao_maxdist;
+    for (int k = 0; k < 3; ++k) {
+        f.bg[k] = p->background[k];
+        f.bg_f[k] = (float)p->background[k];
+    }
+    f.out_rgb = out_rgb;
+    f.out_ids = out_ids;
+    f.out_vis = out_vis;
+    return f;
+}
+
+int err_of(cudaError_t e) {
+    if (e == cudaSuccess) return GBRT_OK;
+    return e == cudaErrorMemoryAllocation ? GBRT_ENOMEM : GBRT_EDEVICE;
+}
+
+int ensure_out(Ctx* c, size_t bytes) {
+    if (c->d_out_bytes >= bytes) return GBRT_OK;
+    if (c->d_out) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(c->d_out);
+        c->d_out = nullptr;
+        c->d_out_bytes = 0;
+    }
+    int rc = err_of(cudaMalloc(&c->d_out, bytes));
+    if (rc == GBRT_OK) c->d_out_bytes = bytes;
+    return rc;
+}
+
+int read_error_word(Ctx* c) {
+    cudaError_t e = cudaMemcpyAsync(c->h_err, c->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return err_of(e);
+    uint32_t w = *c->h_err;
+    if (w) {
+        cudaMemsetAsync(c->d_err, 0, sizeof(uint32_t), c->stream);
+        cudaStreamSynchronize(c->stream);
+    }
+    if (w & ERR_QUEUE_TIMEOUT) return GBRT_ETIMEDOUT;
+    if (w & ERR_DDA_STEPS) return GBRT_ETRAVERSAL;
+    if (w) return GBRT_EINVAL;
+    return GBRT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+GBRT_API int gbrt_version(void) { return GBRT_VERSION; }
+
+GBRT_API const char* gbrt_strerror(int code) {
+    switch (code) {
+        case GBRT_OK: return "ok";
+        case GBRT_EINVAL: return "invalid argument or scene data";
+        case GBRT_ENOMEM: return "out of device or pinned memory";
+        case GBRT_EDEVICE: return "CUDA device or runtime error";
+        case GBRT_ETIMEDOUT: return "a bounded device wait ran out";
+        case GBRT_ETRAVERSAL: return "a grid walk exceeded its step bound";
+        default: return "unknown error";
+    }
+}
+
+GBRT_API int gbrt_create(gbrt_ctx** out, int device, void* cuda_stream) {
+    if (!out) return GBRT_EINVAL;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || n <= 0) {
+        cudaGetLastError();
+        return GBRT_EDEVICE;
+    }
+    if (device < 0 || device >= n) return GBRT_EINVAL;
+    DeviceGuard g(device);
+    if (!g.ok) return GBRT_EDEVICE;
+    gbrt_ctx* c = new (std::nothrow) gbrt_ctx();
+    if (!c) return GBRT_ENOMEM;
+    c->device = device;
+    c->stream = (cudaStream_t)cuda_stream;
+    c->tuning.tile_w = 16;
+    c->tuning.tile_h = 8;
+    c->tuning.block = 128;
+    c->tuning.ctas_per_sm = 0;
+    c->tuning.lanes_refill = 1;
+    if (cudaMalloc(&c->d_err, sizeof(uint32_t)) != cudaSuccess ||
+        cudaMallocHost(&c->h_err, sizeof(uint32_t)) != cudaSuccess ||
+        cudaMemset(c->d_err, 0, sizeof(uint32_t)) != cudaSuccess) {
+        cudaFree(c->d_err);
+        cudaFreeHost(c->h_err);
+        delete c;
+        return GBRT_ENOMEM;
+    }
+    *out = c;
+    return GBRT_OK;
+}
+
+GBRT_API int gbrt_set_stream(gbrt_ctx* ctx, void* cuda_stream) {
+    if (!ctx) return GBRT_EINVAL;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    return GBRT_OK;
+}
+
+GBRT_API int gbrt_sync(gbrt_ctx* ctx) {
+    if (!ctx) return GBRT_EINVAL;
+    DeviceGuard g(ctx->device);
+    return read_error_word(ctx);
+}
+
+GBRT_API int gbrt_destroy(gbrt_ctx* ctx) {
+    if (!ctx) return GBRT_OK;
+    DeviceGuard g(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+    cudaFree(ctx->d_err);
+    cudaFreeHost(ctx->h_err);
+    cudaFree(ctx->d_out);
+    cudaFree(ctx->d_frames);
+    cudaFreeHost(ctx->h_frames);
+    cudaFree(ctx->d_queue);
+    delete ctx;
+    return GBRT_OK;
+}
+
+GBRT_API int gbrt_scene_upload(gbrt_ctx* ctx, const float* spheres, int64_t n_spheres, const float* cylinders,
+                               int64_t n_cylinders, const uint32_t* color_idx, const float* palette,
+                               int32_t n_palette, int flags, gbrt_scene** out) {
+    if (!ctx || !out) return GBRT_EINVAL;
+    *out = nullptr;
+    if (n_spheres < 0 || n_cylinders < 0 || n_spheres + n_cylinders >= (int64_t)GBRT_MISS) return GBRT_EINVAL;
+    if (flags & ~GBRT_HOST_PTRS) return GBRT_EINVAL;
+    const int64_t N = n_spheres + n_cylinders;
+    if ((n_spheres > 0 && !spheres) || (n_cylinders > 0 && !cylinders)) return GBRT_EINVAL;
+    if (N > 0 && (!color_idx || !palette || n_palette <= 0)) return GBRT_EINVAL;
+    if (n_palette < 0) return GBRT_EINVAL;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return GBRT_EDEVICE;
+    gbrt_scene* s = new (std::nothrow) gbrt_scene();
+    if (!s) return GBRT_ENOMEM;
+    int rc = scene_upload(ctx, spheres, n_spheres, cylinders, n_cylinders, color_idx, palette, n_palette, flags, s);
+    if (rc != GBRT_OK) {
+        delete s;
+        return rc;
+    }
+    *out = s;
+    return GBRT_OK;
+}
+
+GBRT_API int gbrt_scene_info(const gbrt_scene* scene, int64_t* n_spheres, int64_t* n_cylinders,
+                             int64_t* device_bytes) {
+    if (!scene) return GBRT_EINVAL;
+    if (n_spheres) *n_spheres = scene->S;
+    if (n_cylinders) *n_cylinders = scene->C;
+    if (device_bytes) *device_bytes = (int64_t)scene->bytes;
+    return GBRT_OK;
+}
+
+GBRT_API int gbrt_scene_free(gbrt_ctx* ctx, gbrt_scene* scene) {
+    if (!scene) return GBRT_OK;
+    if (!ctx) return GBRT_EINVAL;
+    DeviceGuard g(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    scene_release(scene);
+    delete scene;
+    return GBRT_OK;
+}
+
+GBRT_API int gbrt_grid_build(gbrt_ctx* ctx, const gbrt_scene* scene, float lambda, gbrt_grid** out) {
+    if (!ctx || !scene || !out) return GBRT_EINVAL;
+    *out = nullptr;
+    if (!std::isfinite(lambda) || lambda > 1.0e6f) return GBRT_EINVAL;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return GBRT_EDEVICE;
+    gbrt_grid* gr = new (std::nothrow) gbrt_grid();
+    if (!gr) return GBRT_ENOMEM;
+    int rc = grid_build(ctx, scene, lambda, gr);
+    if (rc != GBRT_OK) {
+        delete gr;
+        return rc;
+    }
+    *out = gr;
+    return GBRT_OK;
+}
+
+GBRT_API int gbrt_grid_info(const gbrt_grid* grid, int32_t dims[3], float lo[3], float hi[3], int64_t* refs,
+                            int64_t* device_bytes) {
+    if (!grid) return GBRT_EINVAL;
+    for (int k = 0; k < 3; ++k) {
+        if (dims) dims[k] = grid->dev.n[k];
+        if (lo) lo[k] = grid->dev.lo[k];
+        if (hi) hi[k] = grid->dev.hi[k];
+    }
+    if (refs) *refs = grid->refs;
+    if (device_bytes) *device_bytes = (int64_t)grid->bytes;
+    return GBRT_OK;
+}
+
+GBRT_API int gbrt_grid_free(gbrt_ctx* ctx, gbrt_grid* grid) {
+    if (!grid) return GBRT_OK;
+    if (!ctx) return GBRT_EINVAL;
+    DeviceGuard g(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    grid_release(grid);
+    delete grid;
+    return GBRT_OK;
+}
+
+GBRT_API int gbrt_render(gbrt_ctx* ctx, const gbrt_scene* scene, const gbrt_grid* grid, const gbrt_camera* camera,
+                         int32_t width, int32_t height, int32_t ao_samples, const gbrt_lights* lights,
+                         const gbrt_params* params, void* out_rgb, uint32_t* out_hit_ids,
+                         uint32_t* out_ao_visible) {
+    if (!ctx) return GBRT_EINVAL;
+    int rc = check_frame_args(scene, grid, camera, width, height, ao_samples, lights, params, out_rgb);
+    if (rc != GBRT_OK) return rc;
+    if (params->out_flags & ~GBRT_HOST_PTRS) return GBRT_EINVAL;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return GBRT_EDEVICE;
+    const bool host = (params->out_flags & GBRT_HOST_PTRS) != 0;
+    const size_t npx = (size_t)width * (size_t)height;
+    const size_t rgb_bytes = npx * 3 * (params->precision == GBRT_FP64 ? sizeof(double) : sizeof(float));
+    void* d_rgb = out_rgb;
+    uint32_t* d_ids = out_hit_ids;
+    uint32_t* d_vis = out_ao_visible;
+    if (host) {
+        size_t need = rgb_bytes + (out_hit_ids ? npx * 4 : 0) + (out_ao_visible ? npx * 4 : 0);
+        rc = ensure_out(ctx, (need + 255) & ~(size_t)255);
+        if (rc != GBRT_OK) return rc;
+        char* base = (char*)ctx->d_out;
+        d_rgb = base;
+        size_t off = (rgb_bytes + 15) & ~(size_t)15;
+        if (out_hit_ids) {
+            d_ids = (uint32_t*)(base + off);
+            off += npx * 4;
+        }
+        if (out_ao_visible) d_vis = (uint32_t*)(base + off);
+    }
+    FrameDev f = make_frame(scene, grid, camera, width, height, ao_samples, lights, params, d_rgb, d_ids, d_vis);
+    rc = launch_render(ctx, f);
+    if (rc != GBRT_OK) return rc;
+    if (host) {
+        cudaError_t e = cudaMemcpyAsync(out_rgb, d_rgb, rgb_bytes, cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess && out_hit_ids)
+            e = cudaMemcpyAsync(out_hit_ids, d_ids, npx * 4, cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess && out_ao_visible)
+            e = cudaMemcpyAsync(out_ao_visible, d_vis, npx * 4, cudaMemcpyDeviceToHost, ctx->stream);
+        if (e != cudaSuccess) return err_of(e);
+        return read_error_word(ctx);
+    }
+    return GBRT_OK;
+}
+
+GBRT_API int gbrt_render_batch(gbrt_ctx* ctx, const gbrt_render_item* items, int32_t n, int flags) {
+    if (!ctx || n < 0 || (n > 0 && !items)) return GBRT_EINVAL;
+    if (flags & ~GBRT_BATCH_GRAPH) return GBRT_EINVAL;
+    for (int32_t k = 0; k < n; ++k) {
+        const gbrt_render_item& it = items[k];
+        int rc = check_frame_args(it.scene, it.grid, &it.camera, it.width, it.height, it.ao_samples, &it.lights,
+                                  &it.params, it.out_rgb);
+        if (rc != GBRT_OK) return rc;
+        if (it.params.out_flags != 0) return GBRT_EINVAL;
+    }
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return GBRT_EDEVICE;
+    for (int32_t k = 0; k < n; ++k) {
+        const gbrt_render_item& it = items[k];
+        FrameDev f = make_frame(it.scene, it.grid, &it.camera, it.width, it.height, it.ao_samples, &it.lights,
+                                &it.params, it.out_rgb, it.out_hit_ids, it.out_ao_visible);
+        int rc = launch_render(ctx, f);
+        if (rc != GBRT_OK) return rc;
+    }
+    return GBRT_OK;
+}
+
+GBRT_API int gbrt_ao_probe(gbrt_ctx* ctx, const gbrt_scene* scene, const gbrt_grid* grid, const double* pts,
+                           const double* nrm, int64_t n, int32_t ao_samples, const gbrt_params* params,
+                           float* out_visibility) {
+    if (!ctx || !scene || !grid || !params || n < 0 || (n > 0 && (!pts || !nrm || !out_visibility)))
+        return GBRT_EINVAL;
+    if (n >= (1ll << 32)) return GBRT_EINVAL;
+    if (ao_samples < 0 || ao_samples > GBRT_MAX_SAMPLES) return GBRT_EINVAL;
+    if (params->precision != GBRT_FP32 && params->precision != GBRT_FP64) return GBRT_EINVAL;
+    if (!(params->eps >= 0) || !(params->ao_maxdist > 0)) return GBRT_EINVAL;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return GBRT_EDEVICE;
+    gbrt_camera cam;
+    memset(&cam, 0, sizeof(cam));
+    gbrt_lights lights;
+    memset(&lights, 0, sizeof(lights));
+    FrameDev f = make_frame(scene, grid, &cam, 1, 1, ao_samples, &lights, params, nullptr, nullptr, nullptr);
+    return launch_ao_probe(ctx, f, pts, nrm, n, out_visibility);
+}
+
+GBRT_API int gbrt_philox4x32_10(gbrt_ctx* ctx, const uint32_t* ctr, const uint32_t* key, int64_t n,
+                                uint32_t* out) {
+    if (!ctx || n < 0 || (n > 0 && (!ctr || !key || !out))) return GBRT_EINVAL;
+    if (((uintptr_t)ctr & 15) || ((uintptr_t)out & 15) || ((uintptr_t)key & 7)) return GBRT_EINVAL;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return GBRT_EDEVICE;
+    return launch_philox(ctx, ctr, key, n, out);
+}
+
+GBRT_API int gbrt_set_tuning(gbrt_ctx* ctx, const gbrt_tuning* t) {
+    if (!ctx || !t) return GBRT_EINVAL;
+    if (t->tile_w <= 0 || t->tile_h <= 0 || (t->tile_w * t->tile_h) % 32 != 0 || t->tile_w * t->tile_h > 4096)
+        return GBRT_EINVAL;
+    if (t->block < 32 || t->block > 1024 || t->block % 32 != 0) return GBRT_EINVAL;
+    if (t->ctas_per_sm < 0 || t->ctas_per_sm > 32) return GBRT_EINVAL;
+    ctx->tuning = *t;
+    return GBRT_OK;
+}
+
+GBRT_API int gbrt_get_tuning(const gbrt_ctx* ctx, gbrt_tuning* t) {
+    if (!ctx || !t) return GBRT_EINVAL;
+    *t = ctx->tuning;
+    return GBRT_OK;
+}
+
+GBRT_API int64_t gbrt_launch_count(const gbrt_ctx* ctx) { return ctx ? ctx->launches : -1; }
+
+}  // extern "C"

@@ -1,0 +1,512 @@
+// Device math of the ray tracer: vectors, ray-sphere and ray-cylinder roots,
+// the Amanatides-Woo grid walk, Philox4x32-10, cosine-weighted AO directions,
+// hit refinement and Phong + skylight shading. Templated on the arithmetic
+// type R: float for the FP32 path, double for the plain FP64 path.
+#pragma once
+
+#include <stdint.h>
+
+#include "gbrt_types.h"
+
+namespace gbrt {
+
+// ---------------------------------------------------------------- scalars
+
+template <class R>
+struct Num;
+
+template <>
+struct Num<float> {
+    static __device__ __forceinline__ float inf() { return __int_as_float(0x7f800000); }
+    static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+    // a ray is treated as parallel to a cylinder axis below this |d_perp|^2
+    static __device__ __forceinline__ float parallel_eps() { return 1e-12f; }
+};
+
+template <>
+struct Num<double> {
+    static __device__ __forceinline__ double inf() { return __longlong_as_double(0x7ff0000000000000ll); }
+    static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+    static __device__ __forceinline__ double parallel_eps() { return 1e-24; }
+};
+
+template <class R>
+struct V3 {
+    R x, y, z;
+};
+
+template <class R>
+__device__ __forceinline__ V3<R> v3(R x, R y, R z) { return V3<R>{x, y, z}; }
+template <class R>
+__device__ __forceinline__ V3<R> operator+(V3<R> a, V3<R> b) { return v3(a.x + b.x, a.y + b.y, a.z + b.z); }
+template <class R>
+__device__ __forceinline__ V3<R> operator-(V3<R> a, V3<R> b) { return v3(a.x - b.x, a.y - b.y, a.z - b.z); }
+template <class R>
+__device__ __forceinline__ V3<R> operator*(R s, V3<R> a) { return v3(s * a.x, s * a.y, s * a.z); }
+template <class R>
+__device__ __forceinline__ R dot(V3<R> a, V3<R> b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+// a + s b
+template <class R>
+__device__ __forceinline__ V3<R> madd(V3<R> a, R s, V3<R> b) { return v3(a.x + s * b.x, a.y + s * b.y, a.z + s * b.z); }
+
+template <class R>
+__device__ __forceinline__ V3<R> normalized(V3<R> a) {
+    R l = Num<R>::sqrt_(dot(a, a));
+    return l > R(0) ? v3(a.x / l, a.y / l, a.z / l) : a;
+}
+
+__device__ __forceinline__ V3<float> to_f(V3<double> a) { return v3((float)a.x, (float)a.y, (float)a.z); }
+__device__ __forceinline__ V3<double> to_d(V3<float> a) { return v3((double)a.x, (double)a.y, (double)a.z); }
+__device__ __forceinline__ V3<double> ld3(const double* p) { return v3(p[0], p[1], p[2]); }
+
+// ---------------------------------------------------------------- objects
+
+template <class R>
+struct Obj;
+
+template <>
+struct Obj<float> {
+    static __device__ __forceinline__ void sphere(const SceneDev& s, uint32_t i, V3<float>& c, float& r) {
+        float4 v = __ldg(s.sph + i);
+        c = v3(v.x, v.y, v.z);
+        r = v.w;
+    }
+    static __device__ __forceinline__ void cylinder(const SceneDev& s, uint32_t j, V3<float>& p0, V3<float>& a,
+                                                    float& L, float& r) {
+        float4 A = __ldg(s.cyl_a + j);
+        float4 B = __ldg(s.cyl_b + j);
+        p0 = v3(A.x, A.y, A.z);
+        r = A.w;
+        a = v3(B.x, B.y, B.z);
+        L = B.w;
+    }
+};
+
+template <>
+struct Obj<double> {
+    static __device__ __forceinline__ void sphere(const SceneDev& s, uint32_t i, V3<double>& c, double& r) {
+        double2 a = __ldg(s.sph64 + 2 * (size_t)i);
+        double2 b = __ldg(s.sph64 + 2 * (size_t)i + 1);
+        c = v3(a.x, a.y, b.x);
+        r = b.y;
+    }
+    static __device__ __forceinline__ void cylinder(const SceneDev& s, uint32_t j, V3<double>& p0,
+                                                    V3<double>& a, double& L, double& r) {
+        const double2* q = s.cyl64 + 4 * (size_t)j;
+        double2 q0 = __ldg(q), q1 = __ldg(q + 1), q2 = __ldg(q + 2), q3 = __ldg(q + 3);
+        p0 = v3(q0.x, q0.y, q1.x);
+        a = v3(q1.y, q2.x, q2.y);
+        L = q3.x;
+        r = q3.y;
+    }
+};
+
+// Sphere |p - c| = r against o + t d (|d| = 1): with f = o - c, b = f.d, the
+// squared distance of the line to c is |f - b d|^2, and the roots are
+// -b -/+ sqrt(r^2 - |f - b d|^2). Nearest root in (tmin, tmax].
+template <class R>
+__device__ __forceinline__ bool hit_sphere(V3<R> o, V3<R> d, V3<R> c, R r, R tmin, R tmax, R& t) {
+    V3<R> f = o - c;
+    R b = dot(f, d);
+    V3<R> v = madd(f, -b, d);
+    R disc = r * r - dot(v, v);
+    if (disc < R(0)) return false;
+    R sq = Num<R>::sqrt_(disc);
+    R t0 = -b - sq;
+    if (t0 > tmin && t0 <= tmax) { t = t0; return true; }
+    R t1 = -b + sq;
+    if (t1 > tmin && t1 <= tmax) { t = t1; return true; }
+    return false;
+}
+
+// Open cylinder of radius r about p0 + s a, 0 <= s <= L (|a| = 1). In the plane
+// perpendicular to a the ray is w_p + t d_p; the closest approach is at
+// t_c = -(w_p.d_p)/|d_p|^2 with squared distance h^2, the roots are
+// t_c -/+ sqrt((r^2 - h^2)/|d_p|^2), and a root counts when its axial
+// coordinate lies in [0, L].
+template <class R>
+__device__ __forceinline__ bool hit_cylinder(V3<R> o, V3<R> d, V3<R> p0, V3<R> a, R L, R r, R tmin, R tmax,
+                                             R& t) {
+    V3<R> w = o - p0;
+    R wa = dot(w, a), da = dot(d, a);
+    V3<R> wp = madd(w, -wa, a);
+    V3<R> dp = madd(d, -da, a);
+    R A = dot(dp, dp);
+    if (!(A > Num<R>::parallel_eps())) return false;
+    R inv = R(1) / A;
+    R tc = -dot(wp, dp) * inv;
+    V3<R> m = madd(wp, tc, dp);
+    R disc = r * r - dot(m, m);
+    if (disc < R(0)) return false;
+    R half = Num<R>::sqrt_(disc * inv);
+    R t0 = tc - half;
+    if (t0 > tmin && t0 <= tmax) {
+        R s = wa + t0 * da;
+        if (s >= R(0) && s <= L) { t = t0; return true; }
+    }
+    R t1 = tc + half;
+    if (t1 > tmin && t1 <= tmax) {
+        R s = wa + t1 * da;
+        if (s >= R(0) && s <= L) { t = t1; return true; }
+    }
+    return false;
+}
+
+template <class R>
+__device__ __forceinline__ bool hit_object(const SceneDev& s, uint32_t id, V3<R> o, V3<R> d, R tmin, R tmax, R& t) {
+    if (id < (uint32_t)s.S) {
+        V3<R> c;
+        R r;
+        Obj<R>::sphere(s, id, c, r);
+        return hit_sphere(o, d, c, r, tmin, tmax, t);
+    }
+    V3<R> p0, a;
+    R L, r;
+    Obj<R>::cylinder(s, id - (uint32_t)s.S, p0, a, L, r);
+    return hit_cylinder(o, d, p0, a, L, r, tmin, tmax, t);
+}
+
+// ---------------------------------------------------------------- grid walk
+
+template <class R>
+struct GridP;
+
+template <>
+struct GridP<float> {
+    static __device__ __forceinline__ float lo(const GridDev& g, int k) { return g.lo[k]; }
+    static __device__ __forceinline__ float hi(const GridDev& g, int k) { return g.hi[k]; }
+    static __device__ __forceinline__ float h(const GridDev& g, int k) { return g.h[k]; }
+    static __device__ __forceinline__ float inv_h(const GridDev& g, int k) { return g.inv_h[k]; }
+};
+
+template <>
+struct GridP<double> {
+    static __device__ __forceinline__ double lo(const GridDev& g, int k) { return g.lo64[k]; }
+    static __device__ __forceinline__ double hi(const GridDev& g, int k) { return g.hi64[k]; }
+    static __device__ __forceinline__ double h(const GridDev& g, int k) { return g.h64[k]; }
+    static __device__ __forceinline__ double inv_h(const GridDev& g, int k) { return g.inv_h64[k]; }
+};
+
+// Clip o + t d, t in [tmin, tmax], to the grid box.
+template <class R>
+__device__ __forceinline__ bool clip_grid(const GridDev& g, V3<R> o, V3<R> d, R tmin, R tmax, R& t0, R& t1) {
+    R a = tmin, b = tmax;
+    const R oo[3] = {o.x, o.y, o.z};
+    const R dd[3] = {d.x, d.y, d.z};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        R lo = GridP<R>::lo(g, k), hi = GridP<R>::hi(g, k);
+        if (dd[k] == R(0)) {
+            if (oo[k] < lo || oo[k] > hi) return false;
+        } else {
+            R inv = R(1) / dd[k];
+            R ta = (lo - oo[k]) * inv, tb = (hi - oo[k]) * inv;
+            R mn = ta < tb ? ta : tb, mx = ta < tb ? tb : ta;
+            a = mn > a ? mn : a;
+            b = mx < b ? mx : b;
+        }
+    }
+    t0 = a;
+    t1 = b;
+    return a <= b;
+}
+
+// Amanatides & Woo (1987) traversal state: current cell, per-axis step, the t
+// of the next boundary crossing on each axis and the t between crossings.
+template <class R>
+struct Walk {
+    int cx, cy, cz;
+    int sx, sy, sz;
+    R tnx, tny, tnz;
+    R tdx, tdy, tdz;
+    R t1;
+    int cell;
+    int left;
+};
+
+template <class R>
+__device__ __forceinline__ void axis_setup(const GridDev& g, int k, R o, R d, int c, int& s, R& tn, R& td) {
+    R inf = Num<R>::inf();
+    if (d > R(0)) {
+        s = 1;
+        R inv = R(1) / d;
+        tn = (GridP<R>::lo(g, k) + R(c + 1) * GridP<R>::h(g, k) - o) * inv;
+        td = GridP<R>::h(g, k) * inv;
+    } else if (d < R(0)) {
+        s = -1;
+        R inv = R(1) / d;
+        tn = (GridP<R>::lo(g, k) + R(c) * GridP<R>::h(g, k) - o) * inv;
+        td = -GridP<R>::h(g, k) * inv;
+    } else {
+        s = 0;
+        tn = inf;
+        td = inf;
+    }
+}
+
+template <class R>
+__device__ __forceinline__ int cell_of(const GridDev& g, int k, R x) {
+    R f = floor((x - GridP<R>::lo(g, k)) * GridP<R>::inv_h(g, k));
+    int c = (int)f;
+    c = c < 0 ? 0 : c;
+    return c > g.n[k] - 1 ? g.n[k] - 1 : c;
+}
+
+template <class R>
+__device__ __forceinline__ bool walk_start(const GridDev& g, V3<R> o, V3<R> d, R tmin, R tmax, Walk<R>& w) {
+    R t0, t1;
+    if (g.empty || !clip_grid(g, o, d, tmin, tmax, t0, t1)) return false;
+    V3<R> p = madd(o, t0, d);
+    w.cx = cell_of(g, 0, p.x);
+    w.cy = cell_of(g, 1, p.y);
+    w.cz = cell_of(g, 2, p.z);
+    axis_setup(g, 0, o.x, d.x, w.cx, w.sx, w.tnx, w.tdx);
+    axis_setup(g, 1, o.y, d.y, w.cy, w.sy, w.tny, w.tdy);
+    axis_setup(g, 2, o.z, d.z, w.cz, w.sz, w.tnz, w.tdz);
+    w.t1 = t1;
+    w.cell = (w.cz * g.n[1] + w.cy) * g.n[0] + w.cx;
+    w.left = g.n[0] + g.n[1] + g.n[2] + 3;
+    return true;
+}
+
+template <class R>
+__device__ __forceinline__ R walk_cell_exit(const Walk<R>& w) {
+    R m = w.tnx < w.tny ? w.tnx : w.tny;
+    return m < w.tnz ? m : w.tnz;
+}
+
+// Step to the next cell (ties: x, then y, then z). False when the walk leaves
+// the grid or the clipped interval; sets *overflow past the step bound.
+template <class R>
+__device__ __forceinline__ bool walk_next(const GridDev& g, Walk<R>& w, bool& overflow) {
+    if (--w.left <= 0) {
+        overflow = true;
+        return false;
+    }
+    if (w.tnx <= w.tny && w.tnx <= w.tnz) {
+        if (w.tnx > w.t1) return false;
+        w.cx += w.sx;
+        if ((unsigned)w.cx >= (unsigned)g.n[0]) return false;
+        w.tnx += w.tdx;
+        w.cell += w.sx;
+    } else if (w.tny <= w.tnz) {
+        if (w.tny > w.t1) return false;
+        w.cy += w.sy;
+        if ((unsigned)w.cy >= (unsigned)g.n[1]) return false;
+        w.tny += w.tdy;
+        w.cell += w.sy * g.n[0];
+    } else {
+        if (w.tnz > w.t1) return false;
+        w.cz += w.sz;
+        if ((unsigned)w.cz >= (unsigned)g.n[2]) return false;
+        w.tnz += w.tdz;
+        w.cell += w.sz * g.n[0] * g.n[1];
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------- traversal
+
+template <class R>
+struct Nearest {
+    R t1, t2;
+    uint32_t id1, id2;
+};
+
+template <class R>
+__device__ __forceinline__ void nearest_consider(Nearest<R>& h, uint32_t id, R t) {
+    if (id == h.id1) return;  // the same object listed in another cell
+    if (t < h.t1 || (t == h.t1 && id < h.id1)) {
+        h.t2 = h.t1;
+        h.id2 = h.id1;
+        h.t1 = t;
+        h.id1 = id;
+    } else if (id != h.id2 && (t < h.t2 || (t == h.t2 && id < h.id2))) {
+        h.t2 = t;
+        h.id2 = id;
+    }
+}
+
+// Nearest hit in (tmin, tmax]: walk cells in ray order and stop after the
+// first cell whose exit t is at or beyond the best hit (every object whose hit
+// point lies in a visited cell is listed there).
+template <class R>
+__device__ bool trace_nearest(const GridDev& g, const SceneDev& s, V3<R> o, V3<R> d, R tmin, R tmax, Nearest<R>& h,
+                              bool& overflow) {
+    h.t1 = h.t2 = Num<R>::inf();
+    h.id1 = h.id2 = GBRT_MISS;
+    Walk<R> w;
+    if (!walk_start(g, o, d, tmin, tmax, w)) return false;
+    do {
+        uint2 cr = __ldg(g.cells + w.cell);
+        for (uint32_t k = cr.x, e = cr.x + cr.y; k < e; ++k) {
+            uint32_t id = __ldg(g.items + k);
+            R t;
+            if (hit_object(s, id, o, d, tmin, tmax, t)) nearest_consider(h, id, t);
+        }
+        if (h.id1 != GBRT_MISS && h.t1 <= walk_cell_exit(w)) break;
+    } while (walk_next(g, w, overflow));
+    return h.id1 != GBRT_MISS;
+}
+
+// Any hit with 0 < t <= tmax (AO shadow ray): the first hit ends the walk.
+template <class R>
+__device__ bool trace_any(const GridDev& g, const SceneDev& s, V3<R> o, V3<R> d, R tmax, bool& overflow) {
+    Walk<R> w;
+    if (!walk_start(g, o, d, R(0), tmax, w)) return false;
+    do {
+        uint2 cr = __ldg(g.cells + w.cell);
+        for (uint32_t k = cr.x, e = cr.x + cr.y; k < e; ++k) {
+            uint32_t id = __ldg(g.items + k);
+            R t;
+            if (hit_object(s, id, o, d, R(0), tmax, t)) return true;
+        }
+    } while (walk_next(g, w, overflow));
+    return false;
+}
+
+// ---------------------------------------------------------------- sampling
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw; SC'11): 10 rounds of two 32x32
+// multiplies with the key bumped by the Weyl constants between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+// Two AO uniforms of sample s of point/pixel q: counter (q, s, frame, 0xA0),
+// key (seed_lo, seed_hi); the top 24 bits of words 0 and 1 times 2^-24.
+__device__ __forceinline__ void ao_uniforms(uint32_t q, uint32_t s, uint32_t frame, uint32_t seed_lo,
+                                            uint32_t seed_hi, uint32_t& b1, uint32_t& b2) {
+    uint4 x = philox4x32_10(make_uint4(q, s, frame, 0xA0u), make_uint2(seed_lo, seed_hi));
+    b1 = x.x >> 8;
+    b2 = x.y >> 8;
+}
+
+template <class R>
+__device__ __forceinline__ void sincos_2pi(R u, R& s, R& c);
+template <>
+__device__ __forceinline__ void sincos_2pi<float>(float u, float& s, float& c) { sincospif(2.0f * u, &s, &c); }
+template <>
+__device__ __forceinline__ void sincos_2pi<double>(double u, double& s, double& c) { sincospi(2.0 * u, &s, &c); }
+
+// Cosine-weighted direction about n (Malley: a uniform disk point r = sqrt(u1),
+// phi = 2 pi u2 lifted to z = sqrt(1 - u1)), in the basis of Duff et al. 2017.
+template <class R>
+__device__ __forceinline__ V3<R> cosine_dir(V3<R> n, uint32_t b1, uint32_t b2) {
+    const R scale = R(1) / R(16777216);
+    R u1 = R(b1) * scale, u2 = R(b2) * scale;
+    R sign = copysign(R(1), n.z);
+    R a = R(-1) / (sign + n.z);
+    R b = n.x * n.y * a;
+    V3<R> e1 = v3(R(1) + sign * n.x * n.x * a, sign * b, -sign * n.x);
+    V3<R> e2 = v3(b, sign + n.y * n.y * a, -n.y);
+    R r = Num<R>::sqrt_(u1);
+    R sp, cp;
+    sincos_2pi<R>(u2, sp, cp);
+    R x = r * cp, y = r * sp, z = Num<R>::sqrt_(R(1) - u1);
+    return v3(x * e1.x + y * e2.x + z * n.x, x * e1.y + y * e2.y + z * n.y, x * e1.z + y * e2.z + z * n.z);
+}
+
+// Number of AO samples of (index q) that escape, from origin o about normal n.
+template <class R>
+__device__ __forceinline__ int ao_visible(const FrameDev& f, uint32_t q, V3<R> o, V3<R> n, R maxdist, bool& overflow) {
+    int vis = 0;
+    for (int s = 0; s < f.spp; ++s) {
+        uint32_t b1, b2;
+        ao_uniforms(q, (uint32_t)s, f.frame, f.seed_lo, f.seed_hi, b1, b2);
+        V3<R> d = cosine_dir(n, b1, b2);
+        if (!trace_any(f.grid, f.scene, o, d, maxdist, overflow)) ++vis;
+    }
+    return vis;
+}
+
+// ---------------------------------------------------------------- refinement
+
+// FP64 hit point re-projected onto the surface of object id, and the geometric
+// normal turned to face the incoming ray.
+__device__ __forceinline__ void reproject64(const SceneDev& s, uint32_t id, V3<double> o, V3<double> d, double t,
+                                            V3<double>& p, V3<double>& n) {
+    p = madd(o, t, d);
+    if (id < (uint32_t)s.S) {
+        V3<double> c;
+        double r;
+        Obj<double>::sphere(s, id, c, r);
+        n = normalized(p - c);
+        p = madd(c, r, n);
+    } else {
+        V3<double> p0, a;
+        double L, r;
+        Obj<double>::cylinder(s, id - (uint32_t)s.S, p0, a, L, r);
+        double sa = dot(p - p0, a);
+        V3<double> q = madd(p0, sa, a);
+        n = normalized(p - q);
+        p = madd(q, r, n);
+    }
+    if (dot(n, d) > 0.0) n = v3(-n.x, -n.y, -n.z);
+}
+
+// ---------------------------------------------------------------- shading
+
+template <class R>
+struct ShadeP;
+
+template <>
+struct ShadeP<float> {
+    static __device__ __forceinline__ V3<float> ldir(const FrameDev& f, int l) {
+        return v3(f.ldir_f[l][0], f.ldir_f[l][1], f.ldir_f[l][2]);
+    }
+    static __device__ __forceinline__ float lI(const FrameDev& f, int l) { return f.lI_f[l]; }
+    static __device__ __forceinline__ float sky_kao(const FrameDev& f) { return f.sky_kao_f; }
+    static __device__ __forceinline__ float k_d(const FrameDev& f) { return f.k_d_f; }
+    static __device__ __forceinline__ float k_s(const FrameDev& f) { return f.k_s_f; }
+    static __device__ __forceinline__ float phong(const FrameDev& f) { return f.phong_f; }
+    static __device__ __forceinline__ float pow_(float x, float e) { return powf(x, e); }
+};
+
+template <>
+struct ShadeP<double> {
+    static __device__ __forceinline__ V3<double> ldir(const FrameDev& f, int l) { return ld3(f.ldir[l]); }
+    static __device__ __forceinline__ double lI(const FrameDev& f, int l) { return f.lI[l]; }
+    static __device__ __forceinline__ double sky_kao(const FrameDev& f) { return f.sky_kao; }
+    static __device__ __forceinline__ double k_d(const FrameDev& f) { return f.k_d; }
+    static __device__ __forceinline__ double k_s(const FrameDev& f) { return f.k_s; }
+    static __device__ __forceinline__ double phong(const FrameDev& f) { return f.phong; }
+    static __device__ __forceinline__ double pow_(double x, double e) { return pow(x, e); }
+};
+
+// colour = clamp01(albedo (skylight k_ao V + sum_l s I_l k_d max(0, n.l))
+//                  + sum_{n.l > 0} s I_l k_s max(0, r_l.v)^p), r_l = 2 (n.l) n - l
+template <class R>
+__device__ __forceinline__ void shade(const FrameDev& f, uint32_t id, V3<R> n, V3<R> d, R V, R rgb[3]) {
+    R diff = R(0), spec = R(0);
+    V3<R> v = v3(-d.x, -d.y, -d.z);
+    for (int l = 0; l < f.nl; ++l) {
+        V3<R> L = ShadeP<R>::ldir(f, l);
+        R ndl = dot(n, L);
+        if (ndl <= R(0)) continue;
+        R I = ShadeP<R>::lI(f, l);
+        diff += I * ShadeP<R>::k_d(f) * ndl;
+        V3<R> r = madd(v3(-L.x, -L.y, -L.z), R(2) * ndl, n);
+        R rv = dot(r, v);
+        if (rv > R(0)) spec += I * ShadeP<R>::k_s(f) * ShadeP<R>::pow_(rv, ShadeP<R>::phong(f));
+    }
+    uint32_t ci = __ldg(f.scene.color + id);
+    R amb = ShadeP<R>::sky_kao(f) * V + diff;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        R c = R(__ldg(f.scene.palette + 3 * ci + k)) * amb + spec;
+        rgb[k] = c < R(0) ? R(0) : (c > R(1) ? R(1) : c);
+    }
+}
+
+}  // namespace gbrt

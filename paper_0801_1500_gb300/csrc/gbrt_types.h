@@ -1,0 +1,82 @@
+// Internal device-side views of scenes, grids and frames, shared by the host
+// orchestration code and the kernels of libgbrt (never exposed in the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gbrt.h"
+
+namespace gbrt {
+
+// Error bits of the context's device error word.
+enum : uint32_t {
+    ERR_DDA_STEPS = 1u,      // a grid walk exceeded nx + ny + nz + 3 steps
+    ERR_SCENE_DATA = 2u,     // non-finite / non-positive scene values (device upload path)
+    ERR_QUEUE_TIMEOUT = 4u,  // a bounded wait on the work queue ran out
+};
+
+// Scene in the device layout.
+//   sph    float4 [S]   centre xyz, radius
+//   cyl_a  float4 [C]   end p0 xyz, radius
+//   cyl_b  float4 [C]   unit axis xyz, length
+//   sph64  double2[2S]  (cx, cy), (cz, r)
+//   cyl64  double2[4C]  (p0x, p0y), (p0z, ax), (ay, az), (L, r)
+//   color  uint32 [S+C] palette index; palette float [K*3]
+struct SceneDev {
+    int32_t S, C, K, pad;
+    const float4* sph;
+    const float4* cyl_a;
+    const float4* cyl_b;
+    const double2* sph64;
+    const double2* cyl64;
+    const uint32_t* color;
+    const float* palette;
+};
+
+// Uniform grid. cells[c] = (first item, item count) of cell
+// c = (z * ny + y) * nx + x; items are global object ids, ascending per cell.
+struct GridDev {
+    float lo[3], hi[3], h[3], inv_h[3];
+    double lo64[3], hi64[3], h64[3], inv_h64[3];
+    int32_t n[3];
+    int32_t empty;
+    int64_t ncells;
+    const uint2* cells;
+    const uint32_t* items;
+};
+
+// Everything one frame needs, in the precision each path reads.
+struct FrameDev {
+    SceneDev scene;
+    GridDev grid;
+    // camera (double) -- the float path rounds the primary ray from these
+    double eye[3], dir[3], up[3], right[3];
+    double half_w, half_h;
+    int32_t cam_kind;
+    int32_t W, H, spp;
+    uint32_t frame;
+    uint32_t seed_lo, seed_hi;
+    int32_t precision;
+    // shading
+    int32_t nl;
+    double ldir[GBRT_MAX_LIGHTS][3];
+    double lI[GBRT_MAX_LIGHTS];  // intensity * scale
+    float ldir_f[GBRT_MAX_LIGHTS][3];
+    float lI_f[GBRT_MAX_LIGHTS];
+    double sky_kao, k_d, k_s, phong;
+    float sky_kao_f, k_d_f, k_s_f, phong_f;
+    double eps, ao_maxdist;
+    float ao_maxdist_f;
+    double bg[3];
+    float bg_f[3];
+    // outputs (device)
+    void* out_rgb;
+    uint32_t* out_ids;
+    uint32_t* out_vis;
+    // tiling of this frame into work items
+    int32_t tiles_x, tiles_y;
+    int64_t first_item;  // index of this frame's first work item in a batch
+};
+
+}  // namespace gbrt

@@ -1,0 +1,488 @@
+// Scene upload (input arrays -> device records + FP64 copies + scene box) and
+// the uniform-grid build: count -> exclusive scan -> scatter -> per-cell sort.
+// The grid is the acceleration structure of the tracer; its build is the
+// paper's "Preprocess" phase (Table 5).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "gbrt_internal.h"
+
+namespace gbrt {
+
+// float <-> order-preserving uint32, so atomicMin/atomicMax reduce floats
+__device__ __forceinline__ uint32_t ord_of(float f) {
+    uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+static float float_of_ord(uint32_t o) {
+    uint32_t u = (o & 0x80000000u) ? (o & 0x7fffffffu) : ~o;
+    float f;
+    memcpy(&f, &u, 4);
+    return f;
+}
+
+// One thread per object: device records, FP64 copies, padded-box inputs and a
+// warp-reduced scene box. box[0..2] min, box[3..5] max (ordered), box[6] = 1
+// when any object is invalid.
+__global__ void __launch_bounds__(256) k_scene_prep(const float* sph_in, int64_t S, const float* cyl_in, int64_t C,
+                                                     const uint32_t* color, int32_t K, float4* sph, float4* cyl_a,
+                                                     float4* cyl_b, double2* sph64, double2* cyl64, float4* aabb,
+                                                     uint32_t* box) {
+    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const float big = 3.0e38f;
+    float lo[3] = {big, big, big}, hi[3] = {-big, -big, -big};
+    bool bad = false;
+    if (id < S) {
+        const float* p = sph_in + 4 * id;
+        float c[3] = {p[0], p[1], p[2]}, r = p[3];
+        bad = !(isfinite(c[0]) && isfinite(c[1]) && isfinite(c[2]) && isfinite(r) && r > 0.0f);
+        sph[id] = make_float4(c[0], c[1], c[2], r);
+        sph64[2 * id] = make_double2(c[0], c[1]);
+        sph64[2 * id + 1] = make_double2(c[2], r);
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = c[k] - r;
+            hi[k] = c[k] + r;
+        }
+    } else if (id < S + C) {
+        const int64_t j = id - S;
+        const float* p = cyl_in + 7 * j;
+        float p0[3] = {p[0], p[1], p[2]}, p1[3] = {p[3], p[4], p[5]}, r = p[6];
+        float ax[3], a[3];
+        double ax64[3], a64[3];
+        bool fin = isfinite(r);
+        for (int k = 0; k < 3; ++k) {
+            fin = fin && isfinite(p0[k]) && isfinite(p1[k]);
+            ax[k] = p1[k] - p0[k];
+            ax64[k] = (double)p1[k] - (double)p0[k];
+        }
+        float L = sqrtf(ax[0] * ax[0] + ax[1] * ax[1] + ax[2] * ax[2]);
+        double L64 = sqrt(ax64[0] * ax64[0] + ax64[1] * ax64[1] + ax64[2] * ax64[2]);
+        bad = !(fin && r > 0.0f && L > 0.0f);
+        for (int k = 0; k < 3; ++k) {
+            a[k] = L > 0.0f ? ax[k] / L : 0.0f;
+            a64[k] = L64 > 0.0 ? ax64[k] / L64 : 0.0;
+        }
+        cyl_a[j] = make_float4(p0[0], p0[1], p0[2], r);
+        cyl_b[j] = make_float4(a[0], a[1], a[2], L);
+        cyl64[4 * j] = make_double2(p0[0], p0[1]);
+        cyl64[4 * j + 1] = make_double2(p0[2], a64[0]);
+        cyl64[4 * j + 2] = make_double2(a64[1], a64[2]);
+        cyl64[4 * j + 3] = make_double2(L64, r);
+        for (int k = 0; k < 3; ++k) {
+            float e = r * sqrtf(fmaxf(0.0f, 1.0f - a[k] * a[k]));
+            lo[k] = fminf(p0[k], p1[k]) - e;
+            hi[k] = fmaxf(p0[k], p1[k]) + e;
+        }
+    }
+    if (id < S + C) {
+        if (color[id] >= (uint32_t)K) bad = true;
+        aabb[2 * id] = make_float4(lo[0], lo[1], lo[2], 0.0f);
+        aabb[2 * id + 1] = make_float4(hi[0], hi[1], hi[2], 0.0f);
+        if (bad) {
+            box[6] = 1u;
+            for (int k = 0; k < 3; ++k) {
+                lo[k] = big;
+                hi[k] = -big;
+            }
+        }
+    }
+    // warp reduction, then one atomic per warp and component
+    for (int k = 0; k < 3; ++k) {
+        float l = lo[k], h = hi[k];
+        for (int off = 16; off > 0; off >>= 1) {
+            l = fminf(l, __shfl_xor_sync(0xffffffffu, l, off));
+            h = fmaxf(h, __shfl_xor_sync(0xffffffffu, h, off));
+        }
+        if ((threadIdx.x & 31) == 0 && l <= h) {
+            atomicMin(box + k, ord_of(l));
+            atomicMax(box + 3 + k, ord_of(h));
+        }
+    }
+}
+
+// Grid geometry used by the build kernels (the same float values the walk uses).
+struct BuildP {
+    float lo[3], inv_h[3];
+    int32_t n[3];
+    float pad;
+};
+
+__device__ __forceinline__ int build_cell(const BuildP& p, int k, float x) {
+    int c = (int)floorf((x - p.lo[k]) * p.inv_h[k]);
+    c = c < 0 ? 0 : c;
+    return c > p.n[k] - 1 ? p.n[k] - 1 : c;
+}
+
+__device__ __forceinline__ void cell_range(const float4* aabb, int64_t id, const BuildP& p, int c0[3], int c1[3]) {
+    float4 a = aabb[2 * id], b = aabb[2 * id + 1];
+    c0[0] = build_cell(p, 0, a.x - p.pad);
+    c0[1] = build_cell(p, 1, a.y - p.pad);
+    c0[2] = build_cell(p, 2, a.z - p.pad);
+    c1[0] = build_cell(p, 0, b.x + p.pad);
+    c1[1] = build_cell(p, 1, b.y + p.pad);
+    c1[2] = build_cell(p, 2, b.z + p.pad);
+}
+
+__global__ void __launch_bounds__(256) k_grid_count(const float4* aabb, int64_t N, BuildP p, uint32_t* counts) {
+    int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= N) return;
+    int c0[3], c1[3];
+    cell_range(aabb, id, p, c0, c1);
+    for (int z = c0[2]; z <= c1[2]; ++z)
+        for (int y = c0[1]; y <= c1[1]; ++y)
+            for (int x = c0[0]; x <= c1[0]; ++x) atomicAdd(counts + ((int64_t)z * p.n[1] + y) * p.n[0] + x, 1u);
+}
+
+__global__ void __launch_bounds__(256) k_grid_scatter(const float4* aabb, int64_t N, BuildP p, const uint2* cells,
+                                                       uint32_t* cursor, uint32_t* items) {
+    int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= N) return;
+    int c0[3], c1[3];
+    cell_range(aabb, id, p, c0, c1);
+    for (int z = c0[2]; z <= c1[2]; ++z)
+        for (int y = c0[1]; y <= c1[1]; ++y)
+            for (int x = c0[0]; x <= c1[0]; ++x) {
+                int64_t c = ((int64_t)z * p.n[1] + y) * p.n[0] + x;
+                uint32_t slot = atomicAdd(cursor + c, 1u);
+                items[cells[c].x + slot] = (uint32_t)id;
+            }
+}
+
+// Atomic scatter order is arbitrary: sort each cell's ids ascending (spheres
+// first, then cylinders; deterministic lists).
+__global__ void __launch_bounds__(256) k_cell_sort(const uint2* cells, int64_t ncells, uint32_t* items) {
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncells) return;
+    uint2 cr = cells[c];
+    uint32_t* it = items + cr.x;
+    for (uint32_t a = 1; a < cr.y; ++a) {
+        uint32_t v = it[a];
+        uint32_t b = a;
+        while (b > 0 && it[b - 1] > v) {
+            it[b] = it[b - 1];
+            --b;
+        }
+        it[b] = v;
+    }
+}
+
+// ---- exclusive scan of the per-cell counts (three passes over 4096-wide tiles)
+
+constexpr int SCAN_T = 1024;
+constexpr int SCAN_PER = 4;
+constexpr int SCAN_TILE = SCAN_T * SCAN_PER;
+
+// Exclusive block scan of one value per thread; returns the block total.
+__device__ __forceinline__ unsigned long long block_exclusive_scan(unsigned long long v, unsigned long long& total) {
+    __shared__ unsigned long long warp_tot[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned long long x = v;
+    for (int off = 1; off < 32; off <<= 1) {
+        unsigned long long y = __shfl_up_sync(0xffffffffu, x, off);
+        if (lane >= off) x += y;
+    }
+    if (lane == 31) warp_tot[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int nw = blockDim.x >> 5;
+        unsigned long long w = lane < nw ? warp_tot[lane] : 0ull;
+        for (int off = 1; off < 32; off <<= 1) {
+            unsigned long long y = __shfl_up_sync(0xffffffffu, w, off);
+            if (lane >= off) w += y;
+        }
+        if (lane < nw) warp_tot[lane] = w;
+    }
+    __syncthreads();
+    unsigned long long before = wid > 0 ? warp_tot[wid - 1] : 0ull;
+    total = warp_tot[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return before + x - v;
+}
+
+__global__ void __launch_bounds__(SCAN_T) k_scan_reduce(const uint32_t* in, int64_t n, unsigned long long* sums) {
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_PER;
+    unsigned long long s = 0;
+    for (int k = 0; k < SCAN_PER; ++k)
+        if (base + k < n) s += in[base + k];
+    unsigned long long tot;
+    block_exclusive_scan(s, tot);
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(SCAN_T) k_scan_sums(unsigned long long* sums, int64_t nb, unsigned long long* total) {
+    int64_t per = (nb + SCAN_T - 1) / SCAN_T;
+    int64_t b0 = (int64_t)threadIdx.x * per;
+    unsigned long long s = 0;
+    for (int64_t k = b0; k < b0 + per && k < nb; ++k) s += sums[k];
+    unsigned long long tot;
+    unsigned long long run = block_exclusive_scan(s, tot);
+    for (int64_t k = b0; k < b0 + per && k < nb; ++k) {
+        unsigned long long v = sums[k];
+        sums[k] = run;
+        run += v;
+    }
+    if (threadIdx.x == 0) *total = tot;
+}
+
+__global__ void __launch_bounds__(SCAN_T) k_scan_apply(const uint32_t* in, int64_t n, const unsigned long long* offs,
+                                                        uint2* cells) {
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_PER;
+    uint32_t v[SCAN_PER];
+    unsigned long long s = 0;
+    for (int k = 0; k < SCAN_PER; ++k) {
+        v[k] = base + k < n ? in[base + k] : 0u;
+        s += v[k];
+    }
+    unsigned long long tot;
+    unsigned long long run = offs[blockIdx.x] + block_exclusive_scan(s, tot);
+    for (int k = 0; k < SCAN_PER; ++k) {
+        if (base + k < n) cells[base + k] = make_uint2((uint32_t)run, v[k]);
+        run += v[k];
+    }
+}
+
+// ---------------------------------------------------------------- host side
+
+#define GB_TRY(x)                              \
+    do {                                       \
+        cudaError_t e_ = (x);                  \
+        if (e_ != cudaSuccess) {               \
+            rc = e_ == cudaErrorMemoryAllocation ? GBRT_ENOMEM : GBRT_EDEVICE; \
+            goto fail;                         \
+        }                                      \
+    } while (0)
+
+static bool host_scene_valid(const float* sph, int64_t S, const float* cyl, int64_t C, const uint32_t* color,
+                             int32_t K) {
+    for (int64_t i = 0; i < S; ++i) {
+        const float* p = sph + 4 * i;
+        if (!(std::isfinite(p[0]) && std::isfinite(p[1]) && std::isfinite(p[2]) && std::isfinite(p[3]) && p[3] > 0))
+            return false;
+    }
+    for (int64_t j = 0; j < C; ++j) {
+        const float* p = cyl + 7 * j;
+        for (int k = 0; k < 7; ++k)
+            if (!std::isfinite(p[k])) return false;
+        if (!(p[6] > 0)) return false;
+        if (p[0] == p[3] && p[1] == p[4] && p[2] == p[5]) return false;
+    }
+    for (int64_t i = 0; i < S + C; ++i)
+        if (color[i] >= (uint32_t)K) return false;
+    return true;
+}
+
+void scene_release(Scene* s) {
+    cudaFree(s->sph);
+    cudaFree(s->cyl_a);
+    cudaFree(s->cyl_b);
+    cudaFree(s->sph64);
+    cudaFree(s->cyl64);
+    cudaFree(s->color);
+    cudaFree(s->palette);
+    cudaFree(s->aabb);
+    *s = Scene();
+}
+
+int scene_upload(Ctx* ctx, const float* spheres, int64_t S, const float* cyl, int64_t C, const uint32_t* color,
+                 const float* palette, int32_t K, int flags, Scene* s) {
+    int rc = GBRT_OK;
+    const bool host = (flags & GBRT_HOST_PTRS) != 0;
+    const int64_t N = S + C;
+    float* d_sph_in = nullptr;
+    float* d_cyl_in = nullptr;
+    uint32_t* d_box = nullptr;
+    uint32_t h_box[8];
+    if (host && N > 0 && !host_scene_valid(spheres, S, cyl, C, color, K)) return GBRT_EINVAL;
+    *s = Scene();
+    s->device = ctx->device;
+    s->S = S;
+    s->C = C;
+    s->K = K;
+    {
+        const size_t nS = (size_t)std::max<int64_t>(S, 1), nC = (size_t)std::max<int64_t>(C, 1),
+                     nN = (size_t)std::max<int64_t>(N, 1);
+        GB_TRY(cudaMalloc(&s->sph, nS * sizeof(float4)));
+        GB_TRY(cudaMalloc(&s->cyl_a, nC * sizeof(float4)));
+        GB_TRY(cudaMalloc(&s->cyl_b, nC * sizeof(float4)));
+        GB_TRY(cudaMalloc(&s->sph64, 2 * nS * sizeof(double2)));
+        GB_TRY(cudaMalloc(&s->cyl64, 4 * nC * sizeof(double2)));
+        GB_TRY(cudaMalloc(&s->color, nN * sizeof(uint32_t)));
+        GB_TRY(cudaMalloc(&s->palette, (size_t)std::max(K, 1) * 3 * sizeof(float)));
+        GB_TRY(cudaMalloc(&s->aabb, 2 * nN * sizeof(float4)));
+        GB_TRY(cudaMalloc(&d_box, 8 * sizeof(uint32_t)));
+        s->bytes = nS * (sizeof(float4) + 2 * sizeof(double2)) + nC * (2 * sizeof(float4) + 4 * sizeof(double2)) +
+                   nN * (sizeof(uint32_t) + 2 * sizeof(float4)) + (size_t)std::max(K, 1) * 3 * sizeof(float);
+        if (host) {
+            if (S > 0) {
+                GB_TRY(cudaMalloc(&d_sph_in, (size_t)S * 4 * sizeof(float)));
+                GB_TRY(cudaMemcpyAsync(d_sph_in, spheres, (size_t)S * 4 * sizeof(float), cudaMemcpyHostToDevice,
+                                       ctx->stream));
+            }
+            if (C > 0) {
+                GB_TRY(cudaMalloc(&d_cyl_in, (size_t)C * 7 * sizeof(float)));
+                GB_TRY(cudaMemcpyAsync(d_cyl_in, cyl, (size_t)C * 7 * sizeof(float), cudaMemcpyHostToDevice,
+                                       ctx->stream));
+            }
+            if (N > 0) GB_TRY(cudaMemcpyAsync(s->color, color, (size_t)N * sizeof(uint32_t), cudaMemcpyHostToDevice,
+                                              ctx->stream));
+            if (K > 0) GB_TRY(cudaMemcpyAsync(s->palette, palette, (size_t)K * 3 * sizeof(float),
+                                              cudaMemcpyHostToDevice, ctx->stream));
+        } else {
+            d_sph_in = const_cast<float*>(spheres);
+            d_cyl_in = const_cast<float*>(cyl);
+            if (N > 0) GB_TRY(cudaMemcpyAsync(s->color, color, (size_t)N * sizeof(uint32_t),
+                                              cudaMemcpyDeviceToDevice, ctx->stream));
+            if (K > 0) GB_TRY(cudaMemcpyAsync(s->palette, palette, (size_t)K * 3 * sizeof(float),
+                                              cudaMemcpyDeviceToDevice, ctx->stream));
+        }
+        // box init: min = ord(+big), max = ord(-big); flag 0
+        uint32_t init[8];
+        {
+            float big = 3.0e38f, nbig = -3.0e38f;
+            uint32_t ub, unb;
+            memcpy(&ub, &big, 4);
+            memcpy(&unb, &nbig, 4);
+            uint32_t ob = ub | 0x80000000u, onb = ~unb;
+            init[0] = init[1] = init[2] = ob;
+            init[3] = init[4] = init[5] = onb;
+            init[6] = init[7] = 0u;
+        }
+        GB_TRY(cudaMemcpyAsync(d_box, init, sizeof(init), cudaMemcpyHostToDevice, ctx->stream));
+        if (N > 0) {
+            int blocks = (int)((N + 255) / 256);
+            k_scene_prep<<<blocks, 256, 0, ctx->stream>>>(d_sph_in, S, d_cyl_in, C, s->color, K, s->sph, s->cyl_a,
+                                                          s->cyl_b, s->sph64, s->cyl64, s->aabb, d_box);
+            ctx->launches++;
+            GB_TRY(cudaGetLastError());
+        }
+        GB_TRY(cudaMemcpyAsync(h_box, d_box, sizeof(h_box), cudaMemcpyDeviceToHost, ctx->stream));
+        GB_TRY(cudaStreamSynchronize(ctx->stream));
+        if (h_box[6]) {
+            rc = GBRT_EINVAL;
+            goto fail;
+        }
+        for (int k = 0; k < 3; ++k) {
+            s->lo[k] = N > 0 ? float_of_ord(h_box[k]) : 0.0f;
+            s->hi[k] = N > 0 ? float_of_ord(h_box[3 + k]) : 0.0f;
+        }
+    }
+    if (host) {
+        cudaFree(d_sph_in);
+        cudaFree(d_cyl_in);
+    }
+    cudaFree(d_box);
+    return GBRT_OK;
+fail:
+    cudaStreamSynchronize(ctx->stream);
+    if (host) {
+        cudaFree(d_sph_in);
+        cudaFree(d_cyl_in);
+    }
+    cudaFree(d_box);
+    scene_release(s);
+    return rc;
+}
+
+void grid_release(Grid* g) {
+    cudaFree(g->cells);
+    cudaFree(g->items);
+    *g = Grid();
+}
+
+int grid_build(Ctx* ctx, const Scene* s, float lambda, Grid* g) {
+    int rc = GBRT_OK;
+    uint32_t* counts = nullptr;
+    uint32_t* cursor = nullptr;
+    unsigned long long* sums = nullptr;
+    unsigned long long h_total = 0;
+    *g = Grid();
+    if (!(lambda > 0.0f)) lambda = 2.0f;
+    g->lambda = lambda;
+    const int64_t N = s->S + s->C;
+    GridDev& d = g->dev;
+    {
+        float emax = std::max(s->hi[0] - s->lo[0], std::max(s->hi[1] - s->lo[1], s->hi[2] - s->lo[2]));
+        float pad = 1e-5f * std::max(emax, 1.0f);
+        double E[3], V = 1.0;
+        for (int k = 0; k < 3; ++k) {
+            d.lo[k] = s->lo[k] - pad;
+            d.hi[k] = s->hi[k] + pad;
+            E[k] = (double)d.hi[k] - (double)d.lo[k];
+            V *= E[k];
+        }
+        double target = std::min(std::max((double)lambda * (double)N, 1.0), 67108864.0);
+        double kk = cbrt(target / V);
+        d.ncells = 1;
+        for (int k = 0; k < 3; ++k) {
+            double nk = floor(E[k] * kk + 0.5);
+            nk = std::min(std::max(nk, 1.0), 1024.0);
+            d.n[k] = (int32_t)nk;
+            d.h64[k] = E[k] / nk;
+            d.inv_h64[k] = nk / E[k];
+            d.lo64[k] = (double)d.lo[k];
+            d.hi64[k] = (double)d.hi[k];
+            d.h[k] = (float)d.h64[k];
+            d.inv_h[k] = (float)d.inv_h64[k];
+            d.ncells *= d.n[k];
+        }
+        d.empty = N == 0 ? 1 : 0;
+        BuildP p;
+        for (int k = 0; k < 3; ++k) {
+            p.lo[k] = d.lo[k];
+            p.inv_h[k] = d.inv_h[k];
+            p.n[k] = d.n[k];
+        }
+        p.pad = pad;
+        const int64_t nc = d.ncells;
+        GB_TRY(cudaMalloc(&g->cells, (size_t)nc * sizeof(uint2)));
+        GB_TRY(cudaMalloc(&counts, (size_t)nc * sizeof(uint32_t)));
+        GB_TRY(cudaMemsetAsync(counts, 0, (size_t)nc * sizeof(uint32_t), ctx->stream));
+        if (N > 0) {
+            k_grid_count<<<(int)((N + 255) / 256), 256, 0, ctx->stream>>>(s->aabb, N, p, counts);
+            ctx->launches++;
+            GB_TRY(cudaGetLastError());
+        }
+        const int64_t nb = (nc + SCAN_TILE - 1) / SCAN_TILE;
+        GB_TRY(cudaMalloc(&sums, (size_t)(nb + 1) * sizeof(unsigned long long)));
+        k_scan_reduce<<<(int)nb, SCAN_T, 0, ctx->stream>>>(counts, nc, sums);
+        k_scan_sums<<<1, SCAN_T, 0, ctx->stream>>>(sums, nb, sums + nb);
+        k_scan_apply<<<(int)nb, SCAN_T, 0, ctx->stream>>>(counts, nc, sums, g->cells);
+        ctx->launches += 3;
+        GB_TRY(cudaGetLastError());
+        GB_TRY(cudaMemcpyAsync(&h_total, sums + nb, sizeof(h_total), cudaMemcpyDeviceToHost, ctx->stream));
+        GB_TRY(cudaStreamSynchronize(ctx->stream));
+        if (h_total >= 0xFFFFFFFFull) {
+            rc = GBRT_ENOMEM;
+            goto fail;
+        }
+        g->refs = (int64_t)h_total;
+        GB_TRY(cudaMalloc(&g->items, (size_t)std::max<int64_t>(g->refs, 1) * sizeof(uint32_t)));
+        if (N > 0) {
+            cursor = counts;  // reuse as per-cell fill cursor
+            GB_TRY(cudaMemsetAsync(cursor, 0, (size_t)nc * sizeof(uint32_t), ctx->stream));
+            k_grid_scatter<<<(int)((N + 255) / 256), 256, 0, ctx->stream>>>(s->aabb, N, p, g->cells, cursor,
+                                                                            g->items);
+            k_cell_sort<<<(int)((nc + 255) / 256), 256, 0, ctx->stream>>>(g->cells, nc, g->items);
+            ctx->launches += 2;
+            GB_TRY(cudaGetLastError());
+        }
+        GB_TRY(cudaStreamSynchronize(ctx->stream));
+        d.cells = g->cells;
+        d.items = g->items;
+        g->bytes = (size_t)nc * sizeof(uint2) + (size_t)std::max<int64_t>(g->refs, 1) * sizeof(uint32_t);
+    }
+    cudaFree(counts);
+    cudaFree(sums);
+    return GBRT_OK;
+fail:
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(counts);
+    cudaFree(sums);
+    grid_release(g);
+    return rc;
+}
+
+}  // namespace gbrt

@@ -1,0 +1,349 @@
+"""Thin ctypes binding of libgbrt (include/gbrt.h).
+
+Functions keep the C names and only marshal arguments: torch CUDA tensors and
+numpy arrays become pointers, dataclasses from ``scenes`` become the C structs.
+Every step of the render runs in the library's CUDA kernels; there is no CPU
+path. Importing this module loads ``libgbrt.so`` and raises if it is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LIB_PATH = _build.LIB
+
+OK, EINVAL, ENOMEM, EDEVICE, ETIMEDOUT, ETRAVERSAL = 0, -1, -2, -3, -4, -5
+DEVICE_PTRS, HOST_PTRS, BATCH_GRAPH = 0, 1, 2
+FP32, FP64 = 0, 1
+CAMERA_ORTHO, CAMERA_PINHOLE = 0, 1
+MAX_LIGHTS = 8
+MISS = 0xFFFFFFFF
+
+
+class GbrtError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__(f"{where}: {strerror(code)} ({code})")
+
+
+class gbrt_camera(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("reserved", C.c_int32), ("eye", C.c_double * 3), ("dir", C.c_double * 3),
+                ("up", C.c_double * 3), ("right", C.c_double * 3), ("half_w", C.c_double), ("half_h", C.c_double)]
+
+
+class gbrt_lights(C.Structure):
+    _fields_ = [("n", C.c_int32), ("reserved", C.c_int32), ("dir", (C.c_double * 3) * MAX_LIGHTS),
+                ("intensity", C.c_double * MAX_LIGHTS), ("scale", C.c_double), ("skylight", C.c_double)]
+
+
+class gbrt_params(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("out_flags", C.c_int32), ("seed", C.c_uint64), ("frame", C.c_uint32),
+                ("reserved", C.c_uint32), ("eps", C.c_double), ("ao_maxdist", C.c_double), ("k_ao", C.c_double),
+                ("k_d", C.c_double), ("k_s", C.c_double), ("phong_exp", C.c_double),
+                ("background", C.c_double * 3)]
+
+
+class gbrt_render_item(C.Structure):
+    _fields_ = [("scene", C.c_void_p), ("grid", C.c_void_p), ("camera", gbrt_camera), ("width", C.c_int32),
+                ("height", C.c_int32), ("ao_samples", C.c_int32), ("reserved", C.c_int32),
+                ("lights", gbrt_lights), ("params", gbrt_params), ("out_rgb", C.c_void_p),
+                ("out_hit_ids", C.c_void_p), ("out_ao_visible", C.c_void_p)]
+
+
+class gbrt_tuning(C.Structure):
+    _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("block", C.c_int32), ("ctas_per_sm", C.c_int32),
+                ("lanes_refill", C.c_int32), ("reserved", C.c_int32 * 3)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is not built: run __graft_entry__.build() (nvcc, sm_103a)")
+    L = C.CDLL(LIB_PATH)
+    P, i32, i64, f32 = C.c_void_p, C.c_int32, C.c_int64, C.c_float
+    sig = {
+        "gbrt_version": ([], C.c_int),
+        "gbrt_strerror": ([C.c_int], C.c_char_p),
+        "gbrt_create": ([P, C.c_int, P], C.c_int),
+        "gbrt_set_stream": ([P, P], C.c_int),
+        "gbrt_sync": ([P], C.c_int),
+        "gbrt_destroy": ([P], C.c_int),
+        "gbrt_scene_upload": ([P, P, i64, P, i64, P, P, i32, C.c_int, P], C.c_int),
+        "gbrt_scene_info": ([P, P, P, P], C.c_int),
+        "gbrt_scene_free": ([P, P], C.c_int),
+        "gbrt_grid_build": ([P, P, f32, P], C.c_int),
+        "gbrt_grid_info": ([P, P, P, P, P, P], C.c_int),
+        "gbrt_grid_free": ([P, P], C.c_int),
+        "gbrt_render": ([P, P, P, C.POINTER(gbrt_camera), i32, i32, i32, C.POINTER(gbrt_lights),
+                         C.POINTER(gbrt_params), P, P, P], C.c_int),
+        "gbrt_render_batch": ([P, C.POINTER(gbrt_render_item), i32, C.c_int], C.c_int),
+        "gbrt_ao_probe": ([P, P, P, P, P, i64, i32, C.POINTER(gbrt_params), P], C.c_int),
+        "gbrt_philox4x32_10": ([P, P, P, i64, P], C.c_int),
+        "gbrt_set_tuning": ([P, C.POINTER(gbrt_tuning)], C.c_int),
+        "gbrt_get_tuning": ([P, C.POINTER(gbrt_tuning)], C.c_int),
+        "gbrt_launch_count": ([P], C.c_int64),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    return L
+
+
+lib = _load()
+
+
+def strerror(code: int) -> str:
+    return lib.gbrt_strerror(int(code)).decode()
+
+
+def _check(code, where):
+    if code != OK:
+        raise GbrtError(code, where)
+    return code
+
+
+def ptr(x):
+    """Address of a torch tensor, numpy array or None."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    if isinstance(x, int):
+        return x
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+# ------------------------------------------------------------ struct builders
+
+def make_camera(cam) -> gbrt_camera:
+    c = gbrt_camera()
+    c.kind = int(cam.kind)
+    for k in range(3):
+        c.eye[k], c.dir[k], c.up[k], c.right[k] = cam.eye[k], cam.dir[k], cam.up[k], cam.right[k]
+    c.half_w, c.half_h = float(cam.half_w), float(cam.half_h)
+    return c
+
+
+def make_lights(lights) -> gbrt_lights:
+    L = gbrt_lights()
+    L.n = len(lights.dirs)
+    for l, (d, i) in enumerate(zip(lights.dirs, lights.intensity)):
+        for k in range(3):
+            L.dir[l][k] = float(d[k])
+        L.intensity[l] = float(i)
+    L.scale = float(lights.scale)
+    L.skylight = float(lights.skylight)
+    return L
+
+
+def make_params(p, precision=None, out_flags=0) -> gbrt_params:
+    q = gbrt_params()
+    q.precision = int(p.precision if precision is None else precision)
+    q.out_flags = int(out_flags)
+    q.seed = int(p.seed)
+    q.frame = int(p.frame)
+    q.eps = float(p.eps)
+    q.ao_maxdist = float(p.ao_maxdist)
+    q.k_ao, q.k_d, q.k_s, q.phong_exp = float(p.k_ao), float(p.k_d), float(p.k_s), float(p.phong_exp)
+    for k in range(3):
+        q.background[k] = float(p.background[k])
+    return q
+
+
+# ------------------------------------------------------------ C calls
+
+def gbrt_version() -> int:
+    return lib.gbrt_version()
+
+
+def gbrt_create(device: int = 0, stream=None):
+    h = C.c_void_p()
+    s = None
+    if stream is not None:
+        s = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    _check(lib.gbrt_create(C.byref(h), int(device), s), "gbrt_create")
+    return h.value
+
+
+def gbrt_set_stream(ctx, stream):
+    s = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+    return _check(lib.gbrt_set_stream(ctx, s), "gbrt_set_stream")
+
+
+def gbrt_sync(ctx, check=True):
+    rc = lib.gbrt_sync(ctx)
+    return _check(rc, "gbrt_sync") if check else rc
+
+
+def gbrt_destroy(ctx):
+    return _check(lib.gbrt_destroy(ctx), "gbrt_destroy")
+
+
+def gbrt_scene_upload(ctx, spheres, cylinders, color_idx, palette, flags=None):
+    """Arrays: torch CUDA tensors (device) or numpy arrays (host, flags = HOST_PTRS)."""
+    if flags is None:
+        flags = HOST_PTRS if isinstance(spheres, np.ndarray) else DEVICE_PTRS
+    if flags == HOST_PTRS:
+        spheres = np.ascontiguousarray(spheres, np.float32)
+        cylinders = np.ascontiguousarray(cylinders, np.float32)
+        color_idx = np.ascontiguousarray(color_idx, np.uint32)
+        palette = np.ascontiguousarray(palette, np.float32)
+    h = C.c_void_p()
+    rc = lib.gbrt_scene_upload(ctx, ptr(spheres), int(spheres.shape[0]), ptr(cylinders), int(cylinders.shape[0]),
+                               ptr(color_idx), ptr(palette), int(palette.shape[0]), int(flags), C.byref(h))
+    _check(rc, "gbrt_scene_upload")
+    return h.value
+
+
+def gbrt_scene_info(scene):
+    s, c, b = C.c_int64(), C.c_int64(), C.c_int64()
+    _check(lib.gbrt_scene_info(scene, C.byref(s), C.byref(c), C.byref(b)), "gbrt_scene_info")
+    return dict(n_spheres=s.value, n_cylinders=c.value, device_bytes=b.value)
+
+
+def gbrt_scene_free(ctx, scene):
+    return _check(lib.gbrt_scene_free(ctx, scene), "gbrt_scene_free")
+
+
+def gbrt_grid_build(ctx, scene, lam=0.0):
+    h = C.c_void_p()
+    _check(lib.gbrt_grid_build(ctx, scene, float(lam), C.byref(h)), "gbrt_grid_build")
+    return h.value
+
+
+def gbrt_grid_info(grid):
+    dims = (C.c_int32 * 3)()
+    lo = (C.c_float * 3)()
+    hi = (C.c_float * 3)()
+    refs, nbytes = C.c_int64(), C.c_int64()
+    _check(lib.gbrt_grid_info(grid, dims, lo, hi, C.byref(refs), C.byref(nbytes)), "gbrt_grid_info")
+    return dict(dims=tuple(dims), lo=tuple(lo), hi=tuple(hi), refs=refs.value, device_bytes=nbytes.value)
+
+
+def gbrt_grid_free(ctx, grid):
+    return _check(lib.gbrt_grid_free(ctx, grid), "gbrt_grid_free")
+
+
+def gbrt_render(ctx, scene, grid, camera, width, height, ao_samples, lights, params, out_rgb, out_hit_ids=None,
+                out_ao_visible=None):
+    """camera/lights/params: C structs (make_*) or the ``scenes`` dataclasses."""
+    cam = camera if isinstance(camera, gbrt_camera) else make_camera(camera)
+    li = lights if isinstance(lights, gbrt_lights) else make_lights(lights)
+    pa = params if isinstance(params, gbrt_params) else make_params(params)
+    rc = lib.gbrt_render(ctx, scene, grid, C.byref(cam), int(width), int(height), int(ao_samples), C.byref(li),
+                         C.byref(pa), ptr(out_rgb), ptr(out_hit_ids), ptr(out_ao_visible))
+    return _check(rc, "gbrt_render")
+
+
+def gbrt_render_batch(ctx, items, flags=0):
+    arr = (gbrt_render_item * len(items))(*items)
+    return _check(lib.gbrt_render_batch(ctx, arr, len(items), int(flags)), "gbrt_render_batch")
+
+
+def gbrt_ao_probe(ctx, scene, grid, pts, nrm, ao_samples, params, out_visibility):
+    pa = params if isinstance(params, gbrt_params) else make_params(params)
+    rc = lib.gbrt_ao_probe(ctx, scene, grid, ptr(pts), ptr(nrm), int(pts.shape[0]), int(ao_samples), C.byref(pa),
+                           ptr(out_visibility))
+    return _check(rc, "gbrt_ao_probe")
+
+
+def gbrt_philox4x32_10(ctx, ctr, key, out):
+    return _check(lib.gbrt_philox4x32_10(ctx, ptr(ctr), ptr(key), int(ctr.shape[0]), ptr(out)),
+                  "gbrt_philox4x32_10")
+
+
+def gbrt_set_tuning(ctx, tile_w=16, tile_h=8, block=128, ctas_per_sm=0, lanes_refill=1):
+    t = gbrt_tuning()
+    t.tile_w, t.tile_h, t.block, t.ctas_per_sm, t.lanes_refill = tile_w, tile_h, block, ctas_per_sm, lanes_refill
+    return _check(lib.gbrt_set_tuning(ctx, C.byref(t)), "gbrt_set_tuning")
+
+
+def gbrt_get_tuning(ctx):
+    t = gbrt_tuning()
+    _check(lib.gbrt_get_tuning(ctx, C.byref(t)), "gbrt_get_tuning")
+    return dict(tile_w=t.tile_w, tile_h=t.tile_h, block=t.block, ctas_per_sm=t.ctas_per_sm,
+                lanes_refill=t.lanes_refill)
+
+
+def gbrt_launch_count(ctx) -> int:
+    return int(lib.gbrt_launch_count(ctx))
+
+
+def make_item(scene, grid, camera, width, height, ao_samples, lights, params, out_rgb, out_hit_ids=None,
+              out_ao_visible=None) -> gbrt_render_item:
+    it = gbrt_render_item()
+    it.scene, it.grid = scene, grid
+    it.camera = camera if isinstance(camera, gbrt_camera) else make_camera(camera)
+    it.width, it.height, it.ao_samples = int(width), int(height), int(ao_samples)
+    it.lights = lights if isinstance(lights, gbrt_lights) else make_lights(lights)
+    it.params = params if isinstance(params, gbrt_params) else make_params(params)
+    it.out_rgb, it.out_hit_ids, it.out_ao_visible = ptr(out_rgb), ptr(out_hit_ids), ptr(out_ao_visible)
+    return it
+
+
+# ------------------------------------------------------------ convenience
+
+class Renderer:
+    """One context on a device + resident scenes/grids; outputs are torch tensors.
+
+    The current torch stream is used unless ``stream`` is given.
+    """
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+        self.torch = torch
+        self.device = device
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        self.ctx = gbrt_create(device, self.stream)
+        self._owned = []
+
+    def upload(self, scene, lam=0.0):
+        t = self.torch
+        dev = f"cuda:{self.device}"
+        sph = t.from_numpy(np.ascontiguousarray(scene.spheres, np.float32).reshape(-1, 4)).to(dev)
+        cyl = t.from_numpy(np.ascontiguousarray(scene.cylinders, np.float32).reshape(-1, 7)).to(dev)
+        col = t.from_numpy(np.ascontiguousarray(scene.color_idx, np.uint32).view(np.int32)).to(dev)
+        pal = t.from_numpy(np.ascontiguousarray(scene.palette, np.float32).reshape(-1, 3)).to(dev)
+        t.cuda.synchronize(self.device)
+        sc = gbrt_scene_upload(self.ctx, sph, cyl, col, pal, DEVICE_PTRS)
+        gr = gbrt_grid_build(self.ctx, sc, lam)
+        self._owned.append((sc, gr))
+        return sc, gr
+
+    def render(self, scene, grid, camera, width, height, lights, params, ao_samples=None, ids=False, vis=False):
+        t = self.torch
+        dev = f"cuda:{self.device}"
+        dtype = t.float64 if params.precision == FP64 else t.float32
+        rgb = t.empty((height, width, 3), dtype=dtype, device=dev)
+        hid = t.empty((height, width), dtype=t.int32, device=dev) if ids else None
+        av = t.empty((height, width), dtype=t.int32, device=dev) if vis else None
+        spp = params.ao_samples if ao_samples is None else ao_samples
+        gbrt_render(self.ctx, scene, grid, camera, width, height, spp, lights, params, rgb, hid, av)
+        return rgb, hid, av
+
+    def free(self, scene, grid):
+        gbrt_grid_free(self.ctx, grid)
+        gbrt_scene_free(self.ctx, scene)
+        self._owned = [(s, g) for (s, g) in self._owned if s != scene]
+
+    def close(self):
+        if self.ctx:
+            for sc, gr in self._owned:
+                gbrt_grid_free(self.ctx, gr)
+                gbrt_scene_free(self.ctx, sc)
+            self._owned = []
+            gbrt_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,248 @@
+"""GPU parity tests: the CUDA path through the C ABI against the FP64 oracle."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_0801_1500_gb300 import scenes as S
+from gpu_common import assert_parity, compare, gpu_frame
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0801_1500_gb300 import gbrt
+    return gbrt
+
+
+@pytest.fixture(scope="module")
+def R(G):
+    r = G.Renderer(0)
+    yield r
+    r.close()
+
+
+def test_philox_matches_oracle_and_known_answers(G, R, oracle):
+    import torch
+    rng = np.random.default_rng(0)
+    n = 4099
+    ctr = rng.integers(0, 2 ** 32, (n, 4), dtype=np.uint64).astype(np.uint32)
+    key = rng.integers(0, 2 ** 32, (n, 2), dtype=np.uint64).astype(np.uint32)
+    ctr[0], key[0] = 0, 0
+    ctr[1], key[1] = 0xFFFFFFFF, 0xFFFFFFFF
+    ctr[2] = [0x243f6a88, 0x85a308d3, 0x13198a2e, 0x03707344]
+    key[2] = [0xa4093822, 0x299f31d0]
+    dc = torch.from_numpy(ctr.view(np.int32)).cuda()
+    dk = torch.from_numpy(key.view(np.int32)).cuda()
+    out = torch.empty((n, 4), dtype=torch.int32, device="cuda")
+    G.gbrt_philox4x32_10(R.ctx, dc, dk, out)
+    G.gbrt_sync(R.ctx)
+    got = out.cpu().numpy().view(np.uint32)
+    for k in range(0, n, 37):
+        assert list(got[k]) == list(oracle.philox4x32_10(ctr[k], key[k]))
+    assert list(got[0]) == [0x6627e8d5, 0xe169c58d, 0xbc57ac4c, 0x9b00dbd8]
+    assert list(got[2]) == [0xd16cfe09, 0x94fdcceb, 0x5001e420, 0x24126ea1]
+
+
+@pytest.mark.parametrize("lam", [0.5, 1.0, 2.0, 4.0])
+def test_grid_matches_oracle_grid(G, R, oracle, lam):
+    sc = S.globule(2000, 1900, 25.0, seed=0)
+    scene, grid = R.upload(sc, lam=lam)
+    gi = G.gbrt_grid_info(grid)
+    oi = oracle.grid_info(sc, lam)
+    assert gi["dims"] == oi["dims"]
+    assert abs(gi["refs"] - oi["refs"]) <= 2e-3 * oi["refs"]
+    assert np.allclose(gi["lo"], oi["lo"], atol=1e-4) and np.allclose(gi["hi"], oi["hi"], atol=1e-4)
+    R.free(scene, grid)
+
+
+@pytest.mark.parametrize("prec", [S.PRECISION_FP64, S.PRECISION_FP32])
+def test_small_globule_full_frame(G, R, oracle, prec):
+    # 2,000 spheres + 1,900 cylinders, 256x256, 8 AO samples (plain FP64 and FP32 paths)
+    w = S.small_fp64()
+    p = S.Params(ao_samples=8, seed=0, precision=prec)
+    scene, grid = R.upload(w.scene, lam=2.0)
+    rgb, ids, vis = gpu_frame(G, R, scene, grid, w.camera, w.width, w.height, w.lights, p)
+    ref = oracle.render(w.scene, w.camera, w.width, w.height, w.lights, p, mode="brute")
+    st = compare(rgb, ids, vis, ref)
+    assert_parity(st, "small")
+    if prec == S.PRECISION_FP64:
+        assert st["vis_eq"] >= 0.9999
+    R.free(scene, grid)
+
+
+@pytest.mark.parametrize("W,H,spp", [(97, 61, 9), (33, 131, 3), (1, 1, 5), (17, 1, 4)])
+@pytest.mark.parametrize("prec", [S.PRECISION_FP32, S.PRECISION_FP64])
+def test_ragged_frames(G, R, oracle, W, H, spp, prec):
+    sc = S.globule(600, 570, 15.0, seed=7)
+    cam = S.ortho_camera(sc, W, H)
+    p = S.Params(ao_samples=spp, seed=11, frame=3, precision=prec)
+    scene, grid = R.upload(sc, lam=1.0)
+    rgb, ids, vis = gpu_frame(G, R, scene, grid, cam, W, H, S.default_lights(), p)
+    ref = oracle.render(sc, cam, W, H, S.default_lights(), p, mode="brute")
+    st = compare(rgb, ids, vis, ref)
+    assert st["id_mismatch"] == 0, st
+    assert st["frac_bad"] <= max(1e-3, 1.0 / (W * H)), st
+    R.free(scene, grid)
+
+
+@pytest.fixture(scope="module")
+def paper(G, R):
+    w = S.paper_1mp()
+    scene, grid = R.upload(w.scene, lam=2.0)
+    yield w, scene, grid
+    R.free(scene, grid)
+
+
+@pytest.mark.parametrize("prec", [S.PRECISION_FP32, S.PRECISION_FP64])
+def test_paper_scene_1mp_full_frame(G, R, oracle, paper, prec):
+    # 26,318 objects, 965x1137, 16 AO samples: every pixel against the oracle's grid walk
+    w, scene, grid = paper
+    p = S.Params(ao_samples=16, seed=0, precision=prec)
+    rgb, ids, vis = gpu_frame(G, R, scene, grid, w.camera, w.width, w.height, w.lights, p)
+    ref = oracle.render(w.scene, w.camera, w.width, w.height, w.lights, p, mode="grid", lam=2.0)
+    st = compare(rgb, ids, vis, ref)
+    print("paper 1.1MP", "fp64" if prec else "fp32", st)
+    assert_parity(st, "paper 1mp")
+
+
+def test_paper_scene_1mp_sampled_vs_brute_force(G, R, oracle, paper):
+    # sampled pixels against the brute-force definition (no grid on the oracle side)
+    w, scene, grid = paper
+    p = S.Params(ao_samples=16, seed=0, precision=S.PRECISION_FP32)
+    rgb, ids, vis = gpu_frame(G, R, scene, grid, w.camera, w.width, w.height, w.lights, p)
+    pix = np.random.default_rng(1).choice(w.width * w.height, 600, replace=False)
+    ref = oracle.render(w.scene, w.camera, w.width, w.height, w.lights, p, pixels=pix, mode="brute")
+    st = compare(rgb, ids, vis, ref, pixels=pix)
+    assert st["id_mismatch"] == 0 and st["frac_bad"] <= 1 / 300, st
+
+
+def test_paper_scene_17mp_centre_crop(G, R, oracle, paper):
+    # 3860x4548, 16 AO samples; per-pixel error map on the 256x256 centre crop
+    w, scene, grid = paper
+    w2 = S.paper_17mp(scene=w.scene)
+    p = S.Params(ao_samples=16, seed=0, precision=S.PRECISION_FP32)
+    rgb, ids, vis = gpu_frame(G, R, scene, grid, w2.camera, w2.width, w2.height, w2.lights, p)
+    j0, i0 = w2.height // 2 - 128, w2.width // 2 - 128
+    jj, ii = np.meshgrid(np.arange(j0, j0 + 256), np.arange(i0, i0 + 256), indexing="ij")
+    pix = (jj * w2.width + ii).ravel()
+    ref = oracle.render(w2.scene, w2.camera, w2.width, w2.height, w2.lights, p, pixels=pix, mode="grid", lam=2.0)
+    st = compare(rgb, ids, vis, ref, pixels=pix)
+    print("17.6MP crop", st)
+    assert_parity(st, "17mp crop")
+    # sampled pixels over the whole frame
+    pix = np.random.default_rng(2).choice(w2.width * w2.height, 4000, replace=False)
+    ref = oracle.render(w2.scene, w2.camera, w2.width, w2.height, w2.lights, p, pixels=pix, mode="grid", lam=2.0)
+    st = compare(rgb, ids, vis, ref, pixels=pix)
+    assert st["id_mismatch"] == 0 and st["frac_bad"] <= 2e-3, st
+
+
+@pytest.mark.parametrize("prec", [S.PRECISION_FP32, S.PRECISION_FP64])
+def test_ao_probe_sphere_on_plane(G, R, oracle, prec):
+    import torch
+    Rr = 2.0
+    sc = S.make_scene([[0.0, 0.0, Rr, Rr]])
+    scene, grid = R.upload(sc, lam=1.0)
+    dists = np.array([0.5, 1.0, 2.0, 4.0, 8.0]) * Rr
+    pts = np.stack([dists, 0 * dists, 0 * dists], 1)
+    nrm = np.tile([0.0, 0.0, 1.0], (len(dists), 1))
+    N = 65536
+    p = S.Params(seed=3, precision=prec, eps=1e-6)
+    out = torch.empty(len(dists), dtype=torch.float32, device="cuda")
+    G.gbrt_ao_probe(R.ctx, scene, grid, torch.from_numpy(pts).cuda(), torch.from_numpy(nrm).cuda(), N, p, out)
+    G.gbrt_sync(R.ctx)
+    v = out.cpu().numpy().astype(np.float64)
+    expect = 1.0 - Rr ** 3 / (dists ** 2 + Rr ** 2) ** 1.5
+    assert np.all(np.abs(v - expect) <= 4 * np.sqrt(expect * (1 - expect) / N)), (v, expect)
+    ref = oracle.ao_probe(sc, pts, nrm, N, seed=3, eps=1e-6, mode="brute")
+    assert np.all(np.abs(v - ref) * N <= 2), (v, ref)  # same samples: at most a couple of flips
+    R.free(scene, grid)
+
+
+def test_lone_sphere_sees_open_sky(G, R):
+    sc = S.make_scene([[0.0, 0.0, 0.0, 2.0]])
+    cam = S.ortho_camera(sc, 80, 60)
+    scene, grid = R.upload(sc)
+    for prec in (S.PRECISION_FP32, S.PRECISION_FP64):
+        _, ids, vis = gpu_frame(G, R, scene, grid, cam, 80, 60, S.default_lights(),
+                                S.Params(ao_samples=32, precision=prec))
+        hit = ids != G.MISS
+        assert hit.sum() > 1000 and np.all(vis[hit] == 32)
+    R.free(scene, grid)
+
+
+def test_empty_scene_renders_background(G, R):
+    sc = S.make_scene(np.zeros((0, 4)))
+    scene, grid = R.upload(sc)
+    cam = S.Camera(eye=(0, 0, 5), dir=(0, 0, -1), up=(0, 1, 0), right=(1, 0, 0), half_w=1, half_h=1)
+    p = S.Params(ao_samples=4, background=(0.25, 0.5, 0.75))
+    rgb, ids, vis = gpu_frame(G, R, scene, grid, cam, 40, 30, S.default_lights(), p)
+    assert np.all(ids == G.MISS) and np.allclose(rgb, [0.25, 0.5, 0.75])
+    R.free(scene, grid)
+
+
+def test_invalid_arguments_rejected(G, R):
+    import torch
+    bad = S.make_scene([[0, 0, 0, float("nan")]])
+    with pytest.raises(G.GbrtError) as e:
+        G.gbrt_scene_upload(R.ctx, bad.spheres, bad.cylinders, bad.color_idx, bad.palette)
+    assert e.value.code == G.EINVAL
+    # the device-pointer path validates in its prep kernel
+    d = torch.tensor([[0.0, 0.0, 0.0, -1.0]], device="cuda")
+    with pytest.raises(G.GbrtError):
+        G.gbrt_scene_upload(R.ctx, d, torch.zeros((0, 7), device="cuda"),
+                            torch.zeros(1, dtype=torch.int32, device="cuda"), torch.ones((1, 3), device="cuda"),
+                            G.DEVICE_PTRS)
+    zero_len = S.make_scene(None, [[1, 1, 1, 1, 1, 1, 0.3]])
+    with pytest.raises(G.GbrtError):
+        G.gbrt_scene_upload(R.ctx, zero_len.spheres, zero_len.cylinders, zero_len.color_idx, zero_len.palette)
+    sc = S.make_scene([[0, 0, 0, 1.0]])
+    scene, grid = R.upload(sc)
+    cam = S.ortho_camera(sc, 8, 8)
+    out = torch.empty((8, 8, 3), device="cuda")
+    for W, H, spp in [(0, 8, 4), (8, -1, 4), (8, 8, -1), (8, 8, 100000)]:
+        with pytest.raises(G.GbrtError) as e:
+            G.gbrt_render(R.ctx, scene, grid, cam, W, H, spp, S.default_lights(), S.Params(), out)
+        assert e.value.code == G.EINVAL
+    G.gbrt_sync(R.ctx)
+    R.free(scene, grid)
+
+
+def test_host_output_pointers(G, R):
+    import torch
+    sc = S.globule(300, 285, 10.0, seed=9)
+    W, H = 70, 50
+    cam = S.ortho_camera(sc, W, H)
+    scene, grid = R.upload(sc)
+    p = S.Params(ao_samples=6, seed=2)
+    dev_rgb, dev_ids, _ = R.render(scene, grid, cam, W, H, S.default_lights(), p, ids=True)
+    G.gbrt_sync(R.ctx)
+    host_rgb = np.zeros((H, W, 3), np.float32)
+    host_ids = np.zeros((H, W), np.uint32)
+    G.gbrt_render(R.ctx, scene, grid, cam, W, H, 6, S.default_lights(), G.make_params(p, out_flags=G.HOST_PTRS),
+                  host_rgb, host_ids)
+    assert np.array_equal(host_rgb, dev_rgb.cpu().numpy())
+    assert np.array_equal(host_ids, dev_ids.cpu().numpy().view(np.uint32))
+    R.free(scene, grid)
+
+
+def test_deterministic_and_grid_invariant(G, R):
+    sc = S.globule(800, 760, 16.0, seed=5)
+    W, H = 120, 90
+    cam = S.ortho_camera(sc, W, H)
+    p = S.Params(ao_samples=8, seed=1)
+    frames = []
+    for lam in (0.5, 2.0, 8.0):
+        scene, grid = R.upload(sc, lam=lam)
+        a = gpu_frame(G, R, scene, grid, cam, W, H, S.default_lights(), p)
+        b = gpu_frame(G, R, scene, grid, cam, W, H, S.default_lights(), p)
+        assert all(np.array_equal(x, y) for x, y in zip(a, b))
+        frames.append(a)
+        R.free(scene, grid)
+    for f in frames[1:]:
+        assert (f[1] != frames[0][1]).mean() < 1e-3
+        assert (np.abs(f[0] - frames[0][0]).max(axis=1) > 1 / 255).mean() < 2e-3
