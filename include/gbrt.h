@@ -64,7 +64,8 @@ extern "C" {
 #define GBRT_CAMERA_PINHOLE 1
 #define GBRT_MAX_LIGHTS 8
 #define GBRT_MISS 0xFFFFFFFFu    /* hit id of a pixel whose ray hits nothing */
-#define GBRT_MAX_SAMPLES 4096    /* ao_samples bound */
+#define GBRT_MAX_SAMPLES 4096    /* ao_samples bound of a render */
+#define GBRT_MAX_PROBE_SAMPLES (1 << 20) /* ao_samples bound of gbrt_ao_probe */
 #define GBRT_MAX_DIM 65536       /* width/height bound; width*height < 2^31 */
 
 typedef struct gbrt_ctx gbrt_ctx;
@@ -241,7 +242,8 @@ GBRT_API int gbrt_render_batch(gbrt_ctx* ctx, const gbrt_render_item* items, int
  * illumination, as a probe): for point k, `ao_samples` cosine-weighted rays
  * from pts[k] + eps * nrm[k] with Philox counter (k, s, frame, 0xA0);
  * out_visibility[k] = escaped / ao_samples. pts, nrm: float64 [n][3] device,
- * nrm unit. Uses params precision, seed, frame, eps and ao_maxdist. Async. */
+ * nrm unit; ao_samples <= GBRT_MAX_PROBE_SAMPLES. Uses params precision,
+ * seed, frame, eps and ao_maxdist. Async. */
 GBRT_API int gbrt_ao_probe(gbrt_ctx* ctx, const gbrt_scene* scene, const gbrt_grid* grid, const double* pts,
                            const double* nrm, int64_t n, int32_t ao_samples, const gbrt_params* params,
                            float* out_visibility);

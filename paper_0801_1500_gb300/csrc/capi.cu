@@ -371,7 +371,7 @@ GBRT_API int gbrt_ao_probe(gbrt_ctx* ctx, const gbrt_scene* scene, const gbrt_gr
     if (!ctx || !scene || !grid || !params || n < 0 || (n > 0 && (!pts || !nrm || !out_visibility)))
         return GBRT_EINVAL;
     if (n >= (1ll << 32)) return GBRT_EINVAL;
-    if (ao_samples < 0 || ao_samples > GBRT_MAX_SAMPLES) return GBRT_EINVAL;
+    if (ao_samples < 0 || ao_samples > GBRT_MAX_PROBE_SAMPLES) return GBRT_EINVAL;
     if (params->precision != GBRT_FP32 && params->precision != GBRT_FP64) return GBRT_EINVAL;
     if (!(params->eps >= 0) || !(params->ao_maxdist > 0)) return GBRT_EINVAL;
     DeviceGuard g(ctx->device);
