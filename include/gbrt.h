@@ -147,17 +147,21 @@ typedef struct gbrt_render_item {
 } gbrt_render_item;
 
 /* Launch shape of the render kernels, chosen by the autotuner.
- *  tile_w x tile_h  pixels of one work item (tile_w * tile_h a multiple of 32)
- *  block            threads per CTA (multiple of 32, <= 1024)
- *  ctas_per_sm      resident CTAs per SM of the persistent launch (0 = max)
- *  lanes_refill     replace a finished pixel's lane as soon as it finishes
- *                   (1) or only when the whole warp is done (0) */
+ *  tile_w x tile_h  pixels of one primary-ray work item (a warp); the product
+ *                   must be 32
+ *  block            threads per CTA of the persistent kernels (multiple of
+ *                   32, <= 1024)
+ *  ctas_per_sm      resident CTAs per SM of the persistent launches (0 = as
+ *                   many as fit)
+ *  refill           AO lanes: a warp refills its idle lanes with new shadow
+ *                   rays (ballot + popc compaction) once fewer than `refill`
+ *                   of its 32 lanes still hold a ray (1..32) */
 typedef struct gbrt_tuning {
     int32_t tile_w;
     int32_t tile_h;
     int32_t block;
     int32_t ctas_per_sm;
-    int32_t lanes_refill;
+    int32_t refill;
     int32_t reserved[3];
 } gbrt_tuning;
 

@@ -6,6 +6,7 @@
 
 #include <cmath>
 #include <new>
+#include <vector>
 
 #include "gbrt_internal.h"
 
@@ -172,16 +173,24 @@ GBRT_API int gbrt_create(gbrt_ctx** out, int device, void* cuda_stream) {
     if (!c) return GBRT_ENOMEM;
     c->device = device;
     c->stream = (cudaStream_t)cuda_stream;
-    c->tuning.tile_w = 16;
-    c->tuning.tile_h = 8;
-    c->tuning.block = 128;
+    c->tuning.tile_w = 8;
+    c->tuning.tile_h = 4;
+    c->tuning.block = 256;
     c->tuning.ctas_per_sm = 0;
-    c->tuning.lanes_refill = 1;
+    c->tuning.refill = 16;
+    if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        c->num_sms < 1)
+        c->num_sms = 1;
+    if (cudaEventCreateWithFlags(&c->staging_done, cudaEventDisableTiming) != cudaSuccess) {
+        delete c;
+        return GBRT_EDEVICE;
+    }
     if (cudaMalloc(&c->d_err, sizeof(uint32_t)) != cudaSuccess ||
         cudaMallocHost(&c->h_err, sizeof(uint32_t)) != cudaSuccess ||
         cudaMemset(c->d_err, 0, sizeof(uint32_t)) != cudaSuccess) {
         cudaFree(c->d_err);
         cudaFreeHost(c->h_err);
+        cudaEventDestroy(c->staging_done);
         delete c;
         return GBRT_ENOMEM;
     }
@@ -191,6 +200,9 @@ GBRT_API int gbrt_create(gbrt_ctx** out, int device, void* cuda_stream) {
 
 GBRT_API int gbrt_set_stream(gbrt_ctx* ctx, void* cuda_stream) {
     if (!ctx) return GBRT_EINVAL;
+    DeviceGuard g(ctx->device);
+    // work already enqueued reads the context's buffers: drain the old stream
+    cudaStreamSynchronize(ctx->stream);
     ctx->stream = (cudaStream_t)cuda_stream;
     return GBRT_OK;
 }
@@ -206,12 +218,16 @@ GBRT_API int gbrt_destroy(gbrt_ctx* ctx) {
     DeviceGuard g(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+    if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
+    cudaEventDestroy(ctx->staging_done);
     cudaFree(ctx->d_err);
     cudaFreeHost(ctx->h_err);
     cudaFree(ctx->d_out);
-    cudaFree(ctx->d_frames);
-    cudaFreeHost(ctx->h_frames);
-    cudaFree(ctx->d_queue);
+    cudaFree(ctx->d_hits);
+    cudaFree(ctx->d_vis);
+    cudaFree(ctx->d_desc);
+    cudaFreeHost(ctx->h_desc);
+    cudaFree(ctx->d_counters);
     delete ctx;
     return GBRT_OK;
 }
@@ -329,7 +345,7 @@ GBRT_API int gbrt_render(gbrt_ctx* ctx, const gbrt_scene* scene, const gbrt_grid
         if (out_ao_visible) d_vis = (uint32_t*)(base + off);
     }
     FrameDev f = make_frame(scene, grid, camera, width, height, ao_samples, lights, params, d_rgb, d_ids, d_vis);
-    rc = launch_render(ctx, f);
+    rc = render_frames(ctx, &f, 1, false);
     if (rc != GBRT_OK) return rc;
     if (host) {
         cudaError_t e = cudaMemcpyAsync(out_rgb, d_rgb, rgb_bytes, cudaMemcpyDeviceToHost, ctx->stream);
@@ -355,11 +371,17 @@ GBRT_API int gbrt_render_batch(gbrt_ctx* ctx, const gbrt_render_item* items, int
     }
     DeviceGuard g(ctx->device);
     if (!g.ok) return GBRT_EDEVICE;
-    for (int32_t k = 0; k < n; ++k) {
-        const gbrt_render_item& it = items[k];
-        FrameDev f = make_frame(it.scene, it.grid, &it.camera, it.width, it.height, it.ao_samples, &it.lights,
-                                &it.params, it.out_rgb, it.out_hit_ids, it.out_ao_visible);
-        int rc = launch_render(ctx, f);
+    // one wavefront launch sequence per precision present in the batch
+    for (int prec = GBRT_FP32; prec <= GBRT_FP64; ++prec) {
+        std::vector<FrameDev> frames;
+        for (int32_t k = 0; k < n; ++k) {
+            const gbrt_render_item& it = items[k];
+            if (it.params.precision != prec) continue;
+            frames.push_back(make_frame(it.scene, it.grid, &it.camera, it.width, it.height, it.ao_samples,
+                                        &it.lights, &it.params, it.out_rgb, it.out_hit_ids, it.out_ao_visible));
+        }
+        if (frames.empty()) continue;
+        int rc = render_frames(ctx, frames.data(), (int)frames.size(), (flags & GBRT_BATCH_GRAPH) != 0);
         if (rc != GBRT_OK) return rc;
     }
     return GBRT_OK;
@@ -395,10 +417,10 @@ GBRT_API int gbrt_philox4x32_10(gbrt_ctx* ctx, const uint32_t* ctr, const uint32
 
 GBRT_API int gbrt_set_tuning(gbrt_ctx* ctx, const gbrt_tuning* t) {
     if (!ctx || !t) return GBRT_EINVAL;
-    if (t->tile_w <= 0 || t->tile_h <= 0 || (t->tile_w * t->tile_h) % 32 != 0 || t->tile_w * t->tile_h > 4096)
-        return GBRT_EINVAL;
+    if (t->tile_w <= 0 || t->tile_h <= 0 || t->tile_w * t->tile_h != 32) return GBRT_EINVAL;
     if (t->block < 32 || t->block > 1024 || t->block % 32 != 0) return GBRT_EINVAL;
     if (t->ctas_per_sm < 0 || t->ctas_per_sm > 32) return GBRT_EINVAL;
+    if (t->refill < 1 || t->refill > 32) return GBRT_EINVAL;
     ctx->tuning = *t;
     return GBRT_OK;
 }

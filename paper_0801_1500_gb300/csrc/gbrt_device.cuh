@@ -222,6 +222,7 @@ struct Walk {
     R t1;
     int cell;
     int left;
+    int nx, ny, nz;
 };
 
 template <class R>
@@ -264,8 +265,11 @@ __device__ __forceinline__ bool walk_start(const GridDev& g, V3<R> o, V3<R> d, R
     axis_setup(g, 1, o.y, d.y, w.cy, w.sy, w.tny, w.tdy);
     axis_setup(g, 2, o.z, d.z, w.cz, w.sz, w.tnz, w.tdz);
     w.t1 = t1;
-    w.cell = (w.cz * g.n[1] + w.cy) * g.n[0] + w.cx;
-    w.left = g.n[0] + g.n[1] + g.n[2] + 3;
+    w.nx = g.n[0];
+    w.ny = g.n[1];
+    w.nz = g.n[2];
+    w.cell = (w.cz * w.ny + w.cy) * w.nx + w.cx;
+    w.left = w.nx + w.ny + w.nz + 3;
     return true;
 }
 
@@ -278,7 +282,7 @@ __device__ __forceinline__ R walk_cell_exit(const Walk<R>& w) {
 // Step to the next cell (ties: x, then y, then z). False when the walk leaves
 // the grid or the clipped interval; sets *overflow past the step bound.
 template <class R>
-__device__ __forceinline__ bool walk_next(const GridDev& g, Walk<R>& w, bool& overflow) {
+__device__ __forceinline__ bool walk_next(Walk<R>& w, bool& overflow) {
     if (--w.left <= 0) {
         overflow = true;
         return false;
@@ -286,21 +290,21 @@ __device__ __forceinline__ bool walk_next(const GridDev& g, Walk<R>& w, bool& ov
     if (w.tnx <= w.tny && w.tnx <= w.tnz) {
         if (w.tnx > w.t1) return false;
         w.cx += w.sx;
-        if ((unsigned)w.cx >= (unsigned)g.n[0]) return false;
+        if ((unsigned)w.cx >= (unsigned)w.nx) return false;
         w.tnx += w.tdx;
         w.cell += w.sx;
     } else if (w.tny <= w.tnz) {
         if (w.tny > w.t1) return false;
         w.cy += w.sy;
-        if ((unsigned)w.cy >= (unsigned)g.n[1]) return false;
+        if ((unsigned)w.cy >= (unsigned)w.ny) return false;
         w.tny += w.tdy;
-        w.cell += w.sy * g.n[0];
+        w.cell += w.sy * w.nx;
     } else {
         if (w.tnz > w.t1) return false;
         w.cz += w.sz;
-        if ((unsigned)w.cz >= (unsigned)g.n[2]) return false;
+        if ((unsigned)w.cz >= (unsigned)w.nz) return false;
         w.tnz += w.tdz;
-        w.cell += w.sz * g.n[0] * g.n[1];
+        w.cell += w.sz * w.nx * w.ny;
     }
     return true;
 }
@@ -345,7 +349,7 @@ __device__ bool trace_nearest(const GridDev& g, const SceneDev& s, V3<R> o, V3<R
             if (hit_object(s, id, o, d, tmin, tmax, t)) nearest_consider(h, id, t);
         }
         if (h.id1 != GBRT_MISS && h.t1 <= walk_cell_exit(w)) break;
-    } while (walk_next(g, w, overflow));
+    } while (walk_next(w, overflow));
     return h.id1 != GBRT_MISS;
 }
 
@@ -361,7 +365,7 @@ __device__ bool trace_any(const GridDev& g, const SceneDev& s, V3<R> o, V3<R> d,
             R t;
             if (hit_object(s, id, o, d, R(0), tmax, t)) return true;
         }
-    } while (walk_next(g, w, overflow));
+    } while (walk_next(w, overflow));
     return false;
 }
 

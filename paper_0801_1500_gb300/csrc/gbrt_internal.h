@@ -12,6 +12,7 @@ namespace gbrt {
 
 struct Ctx {
     int device = 0;
+    int num_sms = 1;
     cudaStream_t stream = nullptr;
     uint32_t* d_err = nullptr;   // device error word (ERR_* bits)
     uint32_t* h_err = nullptr;   // pinned mirror
@@ -20,15 +21,26 @@ struct Ctx {
     // device buffers for renders whose outputs are host memory
     void* d_out = nullptr;
     size_t d_out_bytes = 0;
-    // batch descriptors / work queue
-    FrameDev* d_frames = nullptr;
-    FrameDev* h_frames = nullptr;  // pinned staging
-    int32_t frames_cap = 0;
-    unsigned long long* d_queue = nullptr;  // [0] next work item, [1] spare
-    // CUDA graph of the last batch shape
+    // wavefront buffers: hit records, escaped-sample counts, descriptors, counters
+    void* d_hits = nullptr;
+    size_t hits_cap = 0;
+    unsigned int* d_vis = nullptr;
+    size_t vis_cap = 0;
+    void* d_desc = nullptr;
+    size_t desc_cap = 0;
+    void* h_desc = nullptr;  // pinned staging of the descriptors
+    size_t h_desc_cap = 0;
+    void* d_counters = nullptr;
+    size_t counters_cap = 0;
+    size_t counters_bytes_used = 0;
+    cudaEvent_t staging_done = nullptr;  // the last descriptor copy has been consumed
+    bool staging_pending = false;
+    // CUDA graph of the last batch layout
+    cudaStream_t capture_stream = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
-    int32_t graph_n = -1;
-    int64_t graph_items = -1;
+    bool graph_valid = false;
+    long long graph_key = 0;
+    BatchDev graph_bd{};
 };
 
 struct Scene {
@@ -80,8 +92,9 @@ void scene_release(Scene* s);
 int grid_build(Ctx* ctx, const Scene* s, float lambda, Grid* out);
 void grid_release(Grid* g);
 
-// render.cu
-int launch_render(Ctx* ctx, const FrameDev& f);
+// render.cu: render n frames of one precision (descriptors filled by the
+// caller; tiling and hit-buffer fields are set here).
+int render_frames(Ctx* ctx, FrameDev* frames, int n, bool use_graph);
 int launch_ao_probe(Ctx* ctx, const FrameDev& f, const double* pts, const double* nrm, int64_t n, float* out);
 int launch_philox(Ctx* ctx, const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out);
 

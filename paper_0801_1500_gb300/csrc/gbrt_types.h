@@ -74,9 +74,34 @@ struct FrameDev {
     void* out_rgb;
     uint32_t* out_ids;
     uint32_t* out_vis;
-    // tiling of this frame into work items
+    // tiling of this frame into primary-ray work items (tile_w x tile_h = 32)
     int32_t tiles_x, tiles_y;
-    int64_t first_item;  // index of this frame's first work item in a batch
+    int64_t hit_base;  // first slot of this frame's region of the hit buffers
+};
+
+// One batch of frames as the render kernels see it (a kernel parameter).
+//   frames    [n] descriptors (device)
+//   tile_off  [n + 1] prefix sums of primary work items (device)
+//   hit_count [n] hits appended by the primary pass, per frame
+//   job_off   [n + 1] prefix sums of AO rays (hits x samples) per frame
+//   hit_off   [n + 1] prefix sums of hits per frame
+//   hits      2 records per hit (FP32: float4 pairs; FP64: 4 double2), at
+//             frames[f].hit_base + h:  (origin xyz, pixel)  (normal xyz, object id)
+//   vis       escaped AO samples per hit slot
+//   queue     [0] next primary work item, [1] next AO ray, [2] next shading item
+struct BatchDev {
+    const FrameDev* frames;
+    const long long* tile_off;
+    unsigned int* hit_count;
+    unsigned long long* job_off;
+    unsigned long long* hit_off;
+    void* hits;
+    unsigned int* vis;
+    unsigned long long* queue;
+    unsigned int* err;
+    int32_t nframes;
+    int32_t tile_w, tile_h;
+    int32_t refill;
 };
 
 }  // namespace gbrt

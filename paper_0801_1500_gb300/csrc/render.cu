@@ -1,9 +1,39 @@
-// Render kernels: primary ray -> nearest hit -> FP64 refinement -> AO shadow
-// rays -> shading, one pixel per thread; plus the AO probe and raw Philox.
+// Render kernels, wavefront style, for one frame or a batch of frames:
+//   k_primary  persistent; each warp pulls a 32-pixel tile of some frame from
+//              an atomic queue, walks the primary rays (nearest hit), refines
+//              the winner in FP64 and appends the hit (AO origin, normal) to
+//              its frame's hit list;
+//   k_ao_plan  prefix sums of hits and AO rays per frame;
+//   k_ao_walk  persistent; each lane holds one AO shadow ray; a warp refills
+//              its idle lanes together (ballot + popc compaction) once fewer
+//              than `refill` lanes still hold a ray, so warps stay full while
+//              walks of very different length finish;
+//   k_shade    one thread per hit: Phong + skylight with V = escaped / spp.
+// Plus the AO probe and the raw Philox kernel.
+#include <string.h>
+
+#include <algorithm>
+#include <type_traits>
+#include <vector>
+
 #include "gbrt_device.cuh"
 #include "gbrt_internal.h"
 
 namespace gbrt {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// Largest f with off[f] <= x (off nondecreasing, x < off[n]).
+template <class T>
+__device__ __forceinline__ int find_frame(const T* off, int n, T x) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= x) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
 
 // Primary ray of pixel (i, j), in FP64 (both paths derive their ray from it).
 __device__ __forceinline__ void primary_ray64(const FrameDev& f, int i, int j, V3<double>& o, V3<double>& d) {
@@ -46,66 +76,257 @@ __device__ __forceinline__ bool nearest_fp32_refined(const FrameDev& f, V3<doubl
     return true;
 }
 
-template <int MODE>
-__device__ __forceinline__ void render_pixel(const FrameDev& f, int i, int j, bool& overflow) {
-    const uint32_t q = (uint32_t)j * (uint32_t)f.W + (uint32_t)i;
-    V3<double> o64, d64;
-    primary_ray64(f, i, j, o64, d64);
-    uint32_t id = GBRT_MISS;
-    double t64 = 0.0;
-    bool hit;
-    if (MODE == GBRT_FP32) {
-        hit = nearest_fp32_refined(f, o64, d64, id, t64, overflow);
-    } else {
-        Nearest<double> h;
-        hit = trace_nearest<double>(f.grid, f.scene, o64, d64, 0.0, Num<double>::inf(), h, overflow);
-        id = h.id1;
-        t64 = h.t1;
-    }
-    uint32_t vis = 0;
-    if (MODE == GBRT_FP32) {
-        float rgb[3] = {f.bg_f[0], f.bg_f[1], f.bg_f[2]};
-        if (hit) {
-            V3<double> p, n;
-            reproject64(f.scene, id, o64, d64, t64, p, n);
-            V3<float> nf = to_f(n);
-            vis = ao_visible<float>(f, q, to_f(madd(p, f.eps, n)), nf, f.ao_maxdist_f, overflow);
-            float V = f.spp > 0 ? (float)vis / (float)f.spp : 1.0f;
-            shade<float>(f, id, nf, to_f(d64), V, rgb);
-        }
-        float* out = (float*)f.out_rgb + 3 * (size_t)q;
-        out[0] = rgb[0];
-        out[1] = rgb[1];
-        out[2] = rgb[2];
-    } else {
-        double rgb[3] = {f.bg[0], f.bg[1], f.bg[2]};
-        if (hit) {
-            V3<double> p, n;
-            reproject64(f.scene, id, o64, d64, t64, p, n);
-            vis = ao_visible<double>(f, q, madd(p, f.eps, n), n, f.ao_maxdist, overflow);
-            double V = f.spp > 0 ? (double)vis / (double)f.spp : 1.0;
-            shade<double>(f, id, n, d64, V, rgb);
-        }
-        double* out = (double*)f.out_rgb + 3 * (size_t)q;
-        out[0] = rgb[0];
-        out[1] = rgb[1];
-        out[2] = rgb[2];
-    }
-    if (f.out_ids) f.out_ids[q] = hit ? id : GBRT_MISS;
-    if (f.out_vis) f.out_vis[q] = vis;
-}
+// Hit records: (AO origin xyz, pixel) and (normal xyz, object id).
+template <class R>
+struct HitIO;
 
-constexpr int TILE_W = 16, TILE_H = 8;
+template <>
+struct HitIO<float> {
+    static __device__ __forceinline__ void store(void* hits, int64_t slot, V3<double> o, V3<double> n, uint32_t q,
+                                                 uint32_t id) {
+        float4* H = (float4*)hits + 2 * slot;
+        H[0] = make_float4((float)o.x, (float)o.y, (float)o.z, __uint_as_float(q));
+        H[1] = make_float4((float)n.x, (float)n.y, (float)n.z, __uint_as_float(id));
+    }
+    static __device__ __forceinline__ void load(const void* hits, int64_t slot, V3<float>& o, V3<float>& n,
+                                                uint32_t& q, uint32_t& id) {
+        const float4* H = (const float4*)hits + 2 * slot;
+        float4 a = H[0], b = H[1];
+        o = v3(a.x, a.y, a.z);
+        q = __float_as_uint(a.w);
+        n = v3(b.x, b.y, b.z);
+        id = __float_as_uint(b.w);
+    }
+};
+
+template <>
+struct HitIO<double> {
+    static __device__ __forceinline__ void store(void* hits, int64_t slot, V3<double> o, V3<double> n, uint32_t q,
+                                                 uint32_t id) {
+        double2* H = (double2*)hits + 4 * slot;
+        H[0] = make_double2(o.x, o.y);
+        H[1] = make_double2(o.z, __longlong_as_double((long long)q));
+        H[2] = make_double2(n.x, n.y);
+        H[3] = make_double2(n.z, __longlong_as_double((long long)id));
+    }
+    static __device__ __forceinline__ void load(const void* hits, int64_t slot, V3<double>& o, V3<double>& n,
+                                                uint32_t& q, uint32_t& id) {
+        const double2* H = (const double2*)hits + 4 * slot;
+        double2 a = H[0], b = H[1], c = H[2], e = H[3];
+        o = v3(a.x, a.y, b.x);
+        q = (uint32_t)__double_as_longlong(b.y);
+        n = v3(c.x, c.y, e.x);
+        id = (uint32_t)__double_as_longlong(e.y);
+    }
+};
+
+template <class R>
+__device__ __forceinline__ R ao_maxdist(const FrameDev& f);
+template <>
+__device__ __forceinline__ float ao_maxdist<float>(const FrameDev& f) { return f.ao_maxdist_f; }
+template <>
+__device__ __forceinline__ double ao_maxdist<double>(const FrameDev& f) { return f.ao_maxdist; }
+
+// ---------------------------------------------------------------- primary pass
 
 template <int MODE>
-__global__ void __launch_bounds__(TILE_W* TILE_H) k_render_tiled(const __grid_constant__ FrameDev f, uint32_t* err) {
-    int i = blockIdx.x * TILE_W + (threadIdx.x % TILE_W);
-    int j = blockIdx.y * TILE_H + (threadIdx.x / TILE_W);
-    if (i >= f.W || j >= f.H) return;
+__global__ void __launch_bounds__(256) k_primary(const __grid_constant__ BatchDev b) {
+    typedef typename std::conditional<MODE == GBRT_FP32, float, double>::type R;
+    const int lane = threadIdx.x & 31;
+    const long long total = b.tile_off[b.nframes];
     bool overflow = false;
-    render_pixel<MODE>(f, i, j, overflow);
-    if (overflow) atomicOr(err, ERR_DDA_STEPS);
+    while (true) {
+        long long item = 0;
+        if (lane == 0) item = (long long)atomicAdd(b.queue, 1ull);
+        item = __shfl_sync(FULL, item, 0);
+        if (item >= total) break;
+        const int f = find_frame(b.tile_off, b.nframes, item);
+        const FrameDev& F = b.frames[f];
+        const long long t = item - b.tile_off[f];
+        const int tx = (int)(t % F.tiles_x), ty = (int)(t / F.tiles_x);
+        const int i = tx * b.tile_w + lane % b.tile_w;
+        const int j = ty * b.tile_h + lane / b.tile_w;
+        const bool inside = i < F.W && j < F.H;
+        V3<double> o64, d64;
+        uint32_t id = GBRT_MISS;
+        double t64 = 0.0;
+        bool hit = false;
+        if (inside) {
+            primary_ray64(F, i, j, o64, d64);
+            if (MODE == GBRT_FP32) {
+                hit = nearest_fp32_refined(F, o64, d64, id, t64, overflow);
+            } else {
+                Nearest<double> h;
+                hit = trace_nearest<double>(F.grid, F.scene, o64, d64, 0.0, Num<double>::inf(), h, overflow);
+                id = h.id1;
+                t64 = h.t1;
+            }
+        }
+        // warp-aggregated append to this frame's hit list
+        const unsigned hm = __ballot_sync(FULL, hit);
+        unsigned base = 0;
+        if (hm) {
+            const int leader = __ffs(hm) - 1;
+            if (lane == leader) base = atomicAdd(b.hit_count + f, (unsigned)__popc(hm));
+            base = __shfl_sync(FULL, base, leader);
+        }
+        if (!inside) continue;
+        const uint32_t q = (uint32_t)j * (uint32_t)F.W + (uint32_t)i;
+        if (hit) {
+            const int64_t slot = F.hit_base + base + __popc(hm & ((1u << lane) - 1u));
+            V3<double> p, n;
+            reproject64(F.scene, id, o64, d64, t64, p, n);
+            HitIO<R>::store(b.hits, slot, madd(p, F.eps, n), n, q, id);
+            b.vis[slot] = 0u;
+            if (F.out_ids) F.out_ids[q] = id;
+        } else {
+            if (MODE == GBRT_FP32) {
+                float* out = (float*)F.out_rgb + 3 * (size_t)q;
+                out[0] = F.bg_f[0];
+                out[1] = F.bg_f[1];
+                out[2] = F.bg_f[2];
+            } else {
+                double* out = (double*)F.out_rgb + 3 * (size_t)q;
+                out[0] = F.bg[0];
+                out[1] = F.bg[1];
+                out[2] = F.bg[2];
+            }
+            if (F.out_ids) F.out_ids[q] = GBRT_MISS;
+            if (F.out_vis) F.out_vis[q] = 0u;
+        }
+    }
+    if (overflow) atomicOr(b.err, ERR_DDA_STEPS);
 }
+
+// Prefix sums of hits and AO rays per frame; resets the AO and shading queues.
+__global__ void k_ao_plan(const __grid_constant__ BatchDev b) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    unsigned long long jobs = 0, hits = 0;
+    b.job_off[0] = 0;
+    b.hit_off[0] = 0;
+    for (int f = 0; f < b.nframes; ++f) {
+        unsigned long long h = b.hit_count[f];
+        hits += h;
+        jobs += h * (unsigned long long)b.frames[f].spp;
+        b.hit_off[f + 1] = hits;
+        b.job_off[f + 1] = jobs;
+    }
+    b.queue[1] = 0;
+    b.queue[2] = 0;
+}
+
+// ---------------------------------------------------------------- AO pass
+
+template <class R>
+__global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDev b) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const unsigned long long total = b.job_off[b.nframes];
+    const int refill = b.refill;
+    bool has = false, exhausted = false, overflow = false;
+    V3<R> o, d;
+    R tmax = R(0);
+    Walk<R> w;
+    uint32_t k = 0, e = 0;
+    int64_t vslot = 0;
+    SceneDev sc;
+    const uint2* cells = nullptr;
+    const uint32_t* items = nullptr;
+    while (true) {
+        const unsigned act = __ballot_sync(FULL, has);
+        if (!exhausted && __popc(act) < refill) {
+            // compaction: the idle lanes of the warp take the next rays together
+            const unsigned idle = ~act;
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(b.queue + 1, (unsigned long long)__popc(idle));
+            base = __shfl_sync(FULL, base, 0);
+            if (base >= total) exhausted = true;
+            if (!has) {
+                const unsigned long long jj = base + __popc(idle & lt);
+                if (jj < total) {
+                    const int f = find_frame(b.job_off, b.nframes, jj);
+                    const FrameDev& F = b.frames[f];
+                    const unsigned long long jl = jj - b.job_off[f];
+                    const uint32_t spp = (uint32_t)F.spp;
+                    const uint32_t h = (uint32_t)(jl / spp);
+                    const uint32_t smp = (uint32_t)(jl - (unsigned long long)h * spp);
+                    vslot = F.hit_base + h;
+                    V3<R> n;
+                    uint32_t q, oid;
+                    HitIO<R>::load(b.hits, vslot, o, n, q, oid);
+                    uint32_t b1, b2;
+                    ao_uniforms(q, smp, F.frame, F.seed_lo, F.seed_hi, b1, b2);
+                    d = cosine_dir(n, b1, b2);
+                    tmax = ao_maxdist<R>(F);
+                    if (walk_start(F.grid, o, d, R(0), tmax, w)) {
+                        sc = F.scene;
+                        cells = F.grid.cells;
+                        items = F.grid.items;
+                        const uint2 cr = __ldg(cells + w.cell);
+                        k = cr.x;
+                        e = cr.x + cr.y;
+                        has = true;
+                    } else {
+                        atomicAdd(b.vis + vslot, 1u);  // leaves the grid at once: escapes
+                    }
+                }
+            }
+        }
+        if (exhausted && __ballot_sync(FULL, has) == 0) break;
+        if (has && k >= e) {
+            // next cell with candidates, or the end of the walk (the ray escapes)
+            bool more;
+            do {
+                more = walk_next(w, overflow);
+                if (!more) break;
+                const uint2 cr = __ldg(cells + w.cell);
+                k = cr.x;
+                e = cr.x + cr.y;
+            } while (k >= e);
+            if (!more) {
+                atomicAdd(b.vis + vslot, 1u);
+                has = false;
+            }
+        }
+        if (has) {
+            const uint32_t id = __ldg(items + k);
+            ++k;
+            R t;
+            if (hit_object(sc, id, o, d, R(0), tmax, t)) has = false;  // occluded: any hit ends the ray
+        }
+    }
+    if (overflow) atomicOr(b.err, ERR_DDA_STEPS);
+}
+
+// ---------------------------------------------------------------- shading
+
+template <class R>
+__global__ void __launch_bounds__(256) k_shade(const __grid_constant__ BatchDev b) {
+    const unsigned long long total = b.hit_off[b.nframes];
+    for (unsigned long long g = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+         g += (unsigned long long)gridDim.x * blockDim.x) {
+        const int f = find_frame(b.hit_off, b.nframes, g);
+        const FrameDev& F = b.frames[f];
+        const int64_t slot = F.hit_base + (int64_t)(g - b.hit_off[f]);
+        V3<R> o, n;
+        uint32_t q, id;
+        HitIO<R>::load(b.hits, slot, o, n, q, id);
+        const uint32_t vis = b.vis[slot];
+        V3<double> o64, d64;
+        primary_ray64(F, (int)(q % (uint32_t)F.W), (int)(q / (uint32_t)F.W), o64, d64);
+        R V = F.spp > 0 ? (R)vis / (R)F.spp : R(1);
+        R rgb[3];
+        V3<R> d = v3((R)d64.x, (R)d64.y, (R)d64.z);
+        shade<R>(F, id, n, d, V, rgb);
+        R* out = (R*)F.out_rgb + 3 * (size_t)q;
+        out[0] = rgb[0];
+        out[1] = rgb[1];
+        out[2] = rgb[2];
+        if (F.out_vis) F.out_vis[q] = vis;
+    }
+}
+
+// ---------------------------------------------------------------- probe, Philox
 
 template <int MODE>
 __global__ void __launch_bounds__(128) k_ao_probe(const __grid_constant__ FrameDev f, const double* pts,
@@ -129,16 +350,178 @@ __global__ void k_philox(const uint4* ctr, const uint2* key, int64_t n, uint4* o
     if (k < n) out[k] = philox4x32_10(ctr[k], key[k]);
 }
 
-// ---------------------------------------------------------------- launchers
+// ---------------------------------------------------------------- host side
 
-int launch_render(Ctx* ctx, const FrameDev& f) {
-    dim3 grid((f.W + TILE_W - 1) / TILE_W, (f.H + TILE_H - 1) / TILE_H);
-    if (f.precision == GBRT_FP32)
-        k_render_tiled<GBRT_FP32><<<grid, TILE_W * TILE_H, 0, ctx->stream>>>(f, ctx->d_err);
-    else
-        k_render_tiled<GBRT_FP64><<<grid, TILE_W * TILE_H, 0, ctx->stream>>>(f, ctx->d_err);
-    ctx->launches++;
-    return cudaGetLastError() == cudaSuccess ? GBRT_OK : GBRT_EDEVICE;
+namespace {
+
+int err_of(cudaError_t e) {
+    if (e == cudaSuccess) return GBRT_OK;
+    return e == cudaErrorMemoryAllocation ? GBRT_ENOMEM : GBRT_EDEVICE;
+}
+
+// Grow a device buffer (the stream is drained first: old work may still read it).
+int grow(Ctx* ctx, void** p, size_t* cap, size_t need) {
+    if (*cap >= need) return GBRT_OK;
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    size_t want = std::max(need, (size_t)4096);
+    int rc = err_of(cudaMalloc(p, want));
+    if (rc == GBRT_OK) *cap = want;
+    ctx->graph_valid = false;
+    return rc;
+}
+
+template <class K>
+int persistent_grid(Ctx* ctx, K kernel, int block) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, 0) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    if (ctx->tuning.ctas_per_sm > 0) per_sm = std::min(per_sm, ctx->tuning.ctas_per_sm);
+    return per_sm * ctx->num_sms;
+}
+
+}  // namespace
+
+// Lay out one batch (all frames of one precision), upload its descriptors and
+// enqueue memsets + the four kernels on `stream`.
+struct Grids {
+    int primary, ao, shade;
+};
+
+static Grids grids_for(Ctx* ctx, int precision) {
+    const int block = ctx->tuning.block;
+    Grids g;
+    if (precision == GBRT_FP32) {
+        g.primary = persistent_grid(ctx, k_primary<GBRT_FP32>, block);
+        g.ao = persistent_grid(ctx, k_ao_walk<float>, block);
+    } else {
+        g.primary = persistent_grid(ctx, k_primary<GBRT_FP64>, block);
+        g.ao = persistent_grid(ctx, k_ao_walk<double>, block);
+    }
+    g.shade = ctx->num_sms * 8;
+    return g;
+}
+
+static int enqueue_batch(Ctx* ctx, cudaStream_t stream, int precision, const BatchDev& bd, size_t desc_bytes,
+                         const Grids& gr) {
+    cudaError_t e = cudaMemcpyAsync(ctx->d_desc, ctx->h_desc, desc_bytes, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_counters, 0, ctx->counters_bytes_used, stream);
+    if (e != cudaSuccess) return err_of(e);
+    const int block = ctx->tuning.block;
+    if (precision == GBRT_FP32) {
+        k_primary<GBRT_FP32><<<gr.primary, block, 0, stream>>>(bd);
+        k_ao_plan<<<1, 32, 0, stream>>>(bd);
+        k_ao_walk<float><<<gr.ao, block, 0, stream>>>(bd);
+        k_shade<float><<<gr.shade, 256, 0, stream>>>(bd);
+    } else {
+        k_primary<GBRT_FP64><<<gr.primary, block, 0, stream>>>(bd);
+        k_ao_plan<<<1, 32, 0, stream>>>(bd);
+        k_ao_walk<double><<<gr.ao, block, 0, stream>>>(bd);
+        k_shade<double><<<gr.shade, 256, 0, stream>>>(bd);
+    }
+    ctx->launches += 4;
+    return err_of(cudaGetLastError());
+}
+
+int render_frames(Ctx* ctx, FrameDev* frames, int n, bool use_graph) {
+    if (n == 0) return GBRT_OK;
+    const int precision = frames[0].precision;
+    for (int f = 1; f < n; ++f)
+        if (frames[f].precision != precision) return GBRT_EINVAL;
+    const int tw = ctx->tuning.tile_w, th = ctx->tuning.tile_h;
+    const size_t rec = precision == GBRT_FP32 ? 2 * sizeof(float4) : 4 * sizeof(double2);
+    // descriptors: frames, then tile_off (n + 1)
+    const size_t frames_bytes = ((size_t)n * sizeof(FrameDev) + 255) & ~(size_t)255;
+    const size_t desc_bytes = frames_bytes + (size_t)(n + 1) * sizeof(long long);
+    // counters: queue [4], hit_count [n], job_off [n + 1], hit_off [n + 1]
+    const size_t counters_bytes = 4 * sizeof(unsigned long long) + (size_t)n * sizeof(unsigned) +
+                                  2 * (size_t)(n + 1) * sizeof(unsigned long long) + 64;
+    int64_t px = 0;
+    long long tiles = 0;
+    for (int f = 0; f < n; ++f) {
+        frames[f].tiles_x = (frames[f].W + tw - 1) / tw;
+        frames[f].tiles_y = (frames[f].H + th - 1) / th;
+        frames[f].hit_base = px;
+        px += (int64_t)frames[f].W * frames[f].H;
+        tiles += (long long)frames[f].tiles_x * frames[f].tiles_y;
+    }
+    int rc;
+    if ((rc = grow(ctx, &ctx->d_hits, &ctx->hits_cap, (size_t)px * rec)) != GBRT_OK) return rc;
+    if ((rc = grow(ctx, (void**)&ctx->d_vis, &ctx->vis_cap, (size_t)px * sizeof(unsigned))) != GBRT_OK) return rc;
+    if ((rc = grow(ctx, &ctx->d_desc, &ctx->desc_cap, desc_bytes)) != GBRT_OK) return rc;
+    if ((rc = grow(ctx, &ctx->d_counters, &ctx->counters_cap, counters_bytes)) != GBRT_OK) return rc;
+    if (ctx->h_desc_cap < desc_bytes) {
+        if (ctx->staging_pending) cudaEventSynchronize(ctx->staging_done);
+        cudaFreeHost(ctx->h_desc);
+        ctx->h_desc = nullptr;
+        ctx->h_desc_cap = 0;
+        if (cudaMallocHost(&ctx->h_desc, desc_bytes) != cudaSuccess) return GBRT_ENOMEM;
+        ctx->h_desc_cap = desc_bytes;
+        ctx->graph_valid = false;
+    }
+    // the pinned staging buffer is read by the previous batch's copy: wait for it
+    if (ctx->staging_pending) cudaEventSynchronize(ctx->staging_done);
+    memcpy(ctx->h_desc, frames, (size_t)n * sizeof(FrameDev));
+    long long* toff = (long long*)((char*)ctx->h_desc + frames_bytes);
+    toff[0] = 0;
+    for (int f = 0; f < n; ++f) toff[f + 1] = toff[f] + (long long)frames[f].tiles_x * frames[f].tiles_y;
+
+    BatchDev bd;
+    bd.frames = (const FrameDev*)ctx->d_desc;
+    bd.tile_off = (const long long*)((char*)ctx->d_desc + frames_bytes);
+    char* cb = (char*)ctx->d_counters;
+    bd.queue = (unsigned long long*)cb;
+    bd.job_off = (unsigned long long*)(cb + 4 * sizeof(unsigned long long));
+    bd.hit_off = bd.job_off + (n + 1);
+    bd.hit_count = (unsigned*)(bd.hit_off + (n + 1));
+    bd.hits = ctx->d_hits;
+    bd.vis = ctx->d_vis;
+    bd.err = ctx->d_err;
+    bd.nframes = n;
+    bd.tile_w = tw;
+    bd.tile_h = th;
+    bd.refill = ctx->tuning.refill;
+    ctx->counters_bytes_used = counters_bytes;
+
+    const Grids gr = grids_for(ctx, precision);
+    if (!use_graph) {
+        rc = enqueue_batch(ctx, ctx->stream, precision, bd, desc_bytes, gr);
+    } else {
+        // replay a captured graph of {copy, memset, 4 kernels} when the batch
+        // layout (buffers, counts, launch shape) is unchanged
+        const long long key = ((long long)n << 40) ^ ((long long)precision << 36) ^ ((long long)gr.primary << 18) ^
+                              (long long)gr.ao ^ ((long long)desc_bytes << 1);
+        if (!ctx->graph_valid || ctx->graph_key != key || memcmp(&ctx->graph_bd, &bd, sizeof(bd)) != 0) {
+            if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+            ctx->graph_exec = nullptr;
+            ctx->graph_valid = false;
+            if (!ctx->capture_stream &&
+                cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking) != cudaSuccess)
+                return GBRT_EDEVICE;
+            cudaGraph_t graph;
+            if (cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+                return GBRT_EDEVICE;
+            int64_t launches0 = ctx->launches;
+            int crc = enqueue_batch(ctx, ctx->capture_stream, precision, bd, desc_bytes, gr);
+            ctx->launches = launches0;
+            cudaError_t ce = cudaStreamEndCapture(ctx->capture_stream, &graph);
+            if (crc != GBRT_OK || ce != cudaSuccess) return crc != GBRT_OK ? crc : GBRT_EDEVICE;
+            ce = cudaGraphInstantiate(&ctx->graph_exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ce != cudaSuccess) return GBRT_EDEVICE;
+            ctx->graph_valid = true;
+            ctx->graph_key = key;
+            ctx->graph_bd = bd;
+        }
+        rc = err_of(cudaGraphLaunch(ctx->graph_exec, ctx->stream));
+        ctx->launches += 4;
+    }
+    if (rc != GBRT_OK) return rc;
+    cudaEventRecord(ctx->staging_done, ctx->stream);
+    ctx->staging_pending = true;
+    return GBRT_OK;
 }
 
 int launch_ao_probe(Ctx* ctx, const FrameDev& f, const double* pts, const double* nrm, int64_t n, float* out) {

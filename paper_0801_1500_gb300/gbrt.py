@@ -57,7 +57,7 @@ class gbrt_render_item(C.Structure):
 
 class gbrt_tuning(C.Structure):
     _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("block", C.c_int32), ("ctas_per_sm", C.c_int32),
-                ("lanes_refill", C.c_int32), ("reserved", C.c_int32 * 3)]
+                ("refill", C.c_int32), ("reserved", C.c_int32 * 3)]
 
 
 def _load():
@@ -259,17 +259,16 @@ def gbrt_philox4x32_10(ctx, ctr, key, out):
                   "gbrt_philox4x32_10")
 
 
-def gbrt_set_tuning(ctx, tile_w=16, tile_h=8, block=128, ctas_per_sm=0, lanes_refill=1):
+def gbrt_set_tuning(ctx, tile_w=8, tile_h=4, block=256, ctas_per_sm=0, refill=16):
     t = gbrt_tuning()
-    t.tile_w, t.tile_h, t.block, t.ctas_per_sm, t.lanes_refill = tile_w, tile_h, block, ctas_per_sm, lanes_refill
+    t.tile_w, t.tile_h, t.block, t.ctas_per_sm, t.refill = tile_w, tile_h, block, ctas_per_sm, refill
     return _check(lib.gbrt_set_tuning(ctx, C.byref(t)), "gbrt_set_tuning")
 
 
 def gbrt_get_tuning(ctx):
     t = gbrt_tuning()
     _check(lib.gbrt_get_tuning(ctx, C.byref(t)), "gbrt_get_tuning")
-    return dict(tile_w=t.tile_w, tile_h=t.tile_h, block=t.block, ctas_per_sm=t.ctas_per_sm,
-                lanes_refill=t.lanes_refill)
+    return dict(tile_w=t.tile_w, tile_h=t.tile_h, block=t.block, ctas_per_sm=t.ctas_per_sm, refill=t.refill)
 
 
 def gbrt_launch_count(ctx) -> int:

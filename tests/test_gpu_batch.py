@@ -1,0 +1,86 @@
+"""Batched rendering: many frames of uneven size through one persistent launch
+sequence (optionally replayed from a CUDA graph) give exactly the solo images."""
+import numpy as np
+import pytest
+
+from paper_0801_1500_gb300 import scenes as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0801_1500_gb300 import gbrt
+    return gbrt
+
+
+def _frames(sc, n):
+    out = []
+    rng = np.random.default_rng(4)
+    sizes = [(64, 48), (33, 17), (128, 96), (1, 1), (97, 61), (40, 40), (200, 30)]
+    for k in range(n):
+        W, H = sizes[k % len(sizes)]
+        spp = int(rng.integers(1, 20))
+        prec = S.PRECISION_FP64 if k % 4 == 3 else S.PRECISION_FP32
+        out.append(dict(W=W, H=H, spp=spp, cam=S.ortho_camera(sc, W, H, angle_deg=37.0 * k),
+                        p=S.Params(ao_samples=spp, seed=k, frame=k, precision=prec)))
+    return out
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_batch_equals_solo(G, graph):
+    import torch
+    sc = S.globule(500, 475, 14.0, seed=2)
+    lights = S.default_lights()
+    with G.Renderer(0) as r:
+        scene, grid = r.upload(sc, lam=2.0)
+        fr = _frames(sc, 9)
+        solo = []
+        for f in fr:
+            rgb, ids, vis = r.render(scene, grid, f["cam"], f["W"], f["H"], lights, f["p"], ids=True, vis=True)
+            solo.append((rgb.clone(), ids.clone(), vis.clone()))
+        outs = []
+        items = []
+        for f in fr:
+            dt = torch.float64 if f["p"].precision == S.PRECISION_FP64 else torch.float32
+            o = (torch.full((f["H"], f["W"], 3), -1, dtype=dt, device="cuda"),
+                 torch.full((f["H"], f["W"]), -7, dtype=torch.int32, device="cuda"),
+                 torch.full((f["H"], f["W"]), -7, dtype=torch.int32, device="cuda"))
+            outs.append(o)
+            items.append(G.make_item(scene, grid, f["cam"], f["W"], f["H"], f["spp"], lights, f["p"], *o))
+        flags = G.BATCH_GRAPH if graph else 0
+        for rep in range(3 if graph else 1):
+            for o in outs:
+                o[0].fill_(-1)
+                o[1].fill_(-7)
+            G.gbrt_render_batch(r.ctx, items, flags)
+            G.gbrt_sync(r.ctx)
+            for (a, b) in zip(solo, outs):
+                for x, y in zip(a, b):
+                    assert torch.equal(x, y)
+
+
+def test_batch_with_two_scenes(G):
+    import torch
+    s1 = S.globule(300, 285, 10.0, seed=1)
+    s2 = S.globule(900, 855, 18.0, seed=2)
+    lights = S.default_lights()
+    with G.Renderer(0) as r:
+        a = r.upload(s1, lam=1.0)
+        b = r.upload(s2, lam=4.0)
+        jobs = [(a, s1, 50, 40, 7), (b, s2, 64, 64, 12), (a, s1, 31, 77, 3), (b, s2, 128, 16, 16)]
+        items, outs, solo = [], [], []
+        for (sg, sc, W, H, spp) in jobs:
+            cam = S.ortho_camera(sc, W, H, 10.0 * spp)
+            p = S.Params(ao_samples=spp, seed=spp)
+            solo.append(r.render(sg[0], sg[1], cam, W, H, lights, p, ids=True)[:2])
+            o = torch.empty((H, W, 3), device="cuda"), torch.empty((H, W), dtype=torch.int32, device="cuda")
+            outs.append(o)
+            items.append(G.make_item(sg[0], sg[1], cam, W, H, spp, lights, p, o[0], o[1]))
+        G.gbrt_render_batch(r.ctx, items)
+        G.gbrt_sync(r.ctx)
+        for (x0, x1), (y0, y1) in zip(solo, outs):
+            assert torch.equal(x0, y0) and torch.equal(x1, y1)
