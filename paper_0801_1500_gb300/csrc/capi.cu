@@ -69,6 +69,21 @@ FrameDev make_frame(const gbrt_scene* scene, const gbrt_grid* grid, const gbrt_c
     }
     f.half_w = cam->half_w;
     f.half_h = cam->half_h;
+    f.inv_w = 1.0 / (double)W;
+    f.inv_h = 1.0 / (double)H;
+    {
+        double l = sqrt(cam->dir[0] * cam->dir[0] + cam->dir[1] * cam->dir[1] + cam->dir[2] * cam->dir[2]);
+        for (int k = 0; k < 3; ++k) {
+            f.dir_unit[k] = cam->dir[k] / l;
+            f.dir_f[k] = (float)f.dir_unit[k];
+            f.up_f[k] = (float)cam->up[k];
+            f.right_f[k] = (float)cam->right[k];
+        }
+    }
+    f.half_w_f = (float)cam->half_w;
+    f.half_h_f = (float)cam->half_h;
+    f.inv_w_f = (float)f.inv_w;
+    f.inv_h_f = (float)f.inv_h;
     f.cam_kind = cam->kind;
     f.W = W;
     f.H = H;

@@ -6,6 +6,8 @@
 
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "gbrt_types.h"
 
 namespace gbrt {
@@ -61,109 +63,90 @@ __device__ __forceinline__ V3<double> ld3(const double* p) { return v3(p[0], p[1
 
 // ---------------------------------------------------------------- objects
 
+// Reciprocal and square root used inside the primitive test: the FP32 path
+// takes the hardware approximations (about 2 ulp), the FP64 path IEEE ones.
+__device__ __forceinline__ float rcp_(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double rcp_(double x) { return 1.0 / x; }
+__device__ __forceinline__ float sqrt_pos(float x) {
+    x = fmaxf(x, 1e-30f);
+    return x * rsqrtf(x);
+}
+__device__ __forceinline__ double sqrt_pos(double x) { return sqrt(fmax(x, 0.0)); }
+
 template <class R>
 struct Obj;
 
 template <>
 struct Obj<float> {
-    static __device__ __forceinline__ void sphere(const SceneDev& s, uint32_t i, V3<float>& c, float& r) {
-        float4 v = __ldg(s.sph + i);
-        c = v3(v.x, v.y, v.z);
-        r = v.w;
-    }
-    static __device__ __forceinline__ void cylinder(const SceneDev& s, uint32_t j, V3<float>& p0, V3<float>& a,
-                                                    float& L, float& r) {
-        float4 A = __ldg(s.cyl_a + j);
-        float4 B = __ldg(s.cyl_b + j);
+    static __device__ __forceinline__ void load(const float4* obj, uint32_t id, V3<float>& p0, V3<float>& a, float& L,
+                                                float& r) {
+        float4 A = __ldg(obj + 2 * (size_t)id);
+        float4 B = __ldg(obj + 2 * (size_t)id + 1);
         p0 = v3(A.x, A.y, A.z);
         r = A.w;
         a = v3(B.x, B.y, B.z);
         L = B.w;
     }
+    static __device__ __forceinline__ const float4* base(const SceneDev& s) { return s.obj; }
 };
 
 template <>
 struct Obj<double> {
-    static __device__ __forceinline__ void sphere(const SceneDev& s, uint32_t i, V3<double>& c, double& r) {
-        double2 a = __ldg(s.sph64 + 2 * (size_t)i);
-        double2 b = __ldg(s.sph64 + 2 * (size_t)i + 1);
-        c = v3(a.x, a.y, b.x);
-        r = b.y;
-    }
-    static __device__ __forceinline__ void cylinder(const SceneDev& s, uint32_t j, V3<double>& p0,
-                                                    V3<double>& a, double& L, double& r) {
-        const double2* q = s.cyl64 + 4 * (size_t)j;
+    static __device__ __forceinline__ void load(const double2* obj, uint32_t id, V3<double>& p0, V3<double>& a,
+                                                double& L, double& r) {
+        const double2* q = obj + 4 * (size_t)id;
         double2 q0 = __ldg(q), q1 = __ldg(q + 1), q2 = __ldg(q + 2), q3 = __ldg(q + 3);
         p0 = v3(q0.x, q0.y, q1.x);
-        a = v3(q1.y, q2.x, q2.y);
-        L = q3.x;
-        r = q3.y;
+        r = q1.y;
+        a = v3(q2.x, q2.y, q3.x);
+        L = q3.y;
     }
+    static __device__ __forceinline__ const double2* base(const SceneDev& s) { return s.obj64; }
 };
 
-// Sphere |p - c| = r against o + t d (|d| = 1): with f = o - c, b = f.d, the
-// squared distance of the line to c is |f - b d|^2, and the roots are
-// -b -/+ sqrt(r^2 - |f - b d|^2). Nearest root in (tmin, tmax].
 template <class R>
-__device__ __forceinline__ bool hit_sphere(V3<R> o, V3<R> d, V3<R> c, R r, R tmin, R tmax, R& t) {
-    V3<R> f = o - c;
-    R b = dot(f, d);
-    V3<R> v = madd(f, -b, d);
-    R disc = r * r - dot(v, v);
-    if (disc < R(0)) return false;
-    R sq = Num<R>::sqrt_(disc);
-    R t0 = -b - sq;
-    if (t0 > tmin && t0 <= tmax) { t = t0; return true; }
-    R t1 = -b + sq;
-    if (t1 > tmin && t1 <= tmax) { t = t1; return true; }
-    return false;
-}
+using ObjPtr = typename std::conditional<std::is_same<R, float>::value, const float4*, const double2*>::type;
 
-// Open cylinder of radius r about p0 + s a, 0 <= s <= L (|a| = 1). In the plane
-// perpendicular to a the ray is w_p + t d_p; the closest approach is at
-// t_c = -(w_p.d_p)/|d_p|^2 with squared distance h^2, the roots are
-// t_c -/+ sqrt((r^2 - h^2)/|d_p|^2), and a root counts when its axial
-// coordinate lies in [0, L].
+// One branch-free test for both primitives. An open cylinder of radius r about
+// p0 + s a, 0 <= s <= L (|a| = 1): in the plane perpendicular to a the ray is
+// w_p + t d_p (w = o - p0); the closest approach is at t_c = -(w_p.d_p)/|d_p|^2
+// with squared distance h^2, the roots are t_c -/+ sqrt((r^2 - h^2)/|d_p|^2),
+// and a root counts when its axial coordinate s = (w + t d).a is in [0, L].
+// With a = 0 and L = 0 the same arithmetic is the ray-sphere test about
+// p0: d_p = d, w_p = o - p0, t_c = -(o - p0).d, h = distance of the line to
+// p0, and s = 0 for both roots. Nearest root in (tmin, tmax].
 template <class R>
-__device__ __forceinline__ bool hit_cylinder(V3<R> o, V3<R> d, V3<R> p0, V3<R> a, R L, R r, R tmin, R tmax,
-                                             R& t) {
+__device__ __forceinline__ bool hit_prim(V3<R> o, V3<R> d, V3<R> p0, V3<R> a, R L, R r, R tmin, R tmax, R& t) {
     V3<R> w = o - p0;
     R wa = dot(w, a), da = dot(d, a);
     V3<R> wp = madd(w, -wa, a);
     V3<R> dp = madd(d, -da, a);
     R A = dot(dp, dp);
-    if (!(A > Num<R>::parallel_eps())) return false;
-    R inv = R(1) / A;
+    R inv = rcp_(A);
     R tc = -dot(wp, dp) * inv;
     V3<R> m = madd(wp, tc, dp);
     R disc = r * r - dot(m, m);
-    if (disc < R(0)) return false;
-    R half = Num<R>::sqrt_(disc * inv);
-    R t0 = tc - half;
-    if (t0 > tmin && t0 <= tmax) {
-        R s = wa + t0 * da;
-        if (s >= R(0) && s <= L) { t = t0; return true; }
-    }
-    R t1 = tc + half;
-    if (t1 > tmin && t1 <= tmax) {
-        R s = wa + t1 * da;
-        if (s >= R(0) && s <= L) { t = t1; return true; }
-    }
-    return false;
+    R half = sqrt_pos(disc * inv);
+    R t0 = tc - half, t1 = tc + half;
+    R s0 = wa + t0 * da, s1 = wa + t1 * da;
+    bool ok = disc >= R(0) && A > Num<R>::parallel_eps();
+    bool h0 = ok && t0 > tmin && t0 <= tmax && s0 >= R(0) && s0 <= L;
+    bool h1 = ok && t1 > tmin && t1 <= tmax && s1 >= R(0) && s1 <= L;
+    t = h0 ? t0 : t1;
+    return h0 || h1;
+}
+
+template <class R>
+__device__ __forceinline__ bool hit_object(ObjPtr<R> obj, uint32_t id, V3<R> o, V3<R> d, R tmin, R tmax, R& t) {
+    V3<R> p0, a;
+    R L, r;
+    Obj<R>::load(obj, id, p0, a, L, r);
+    return hit_prim(o, d, p0, a, L, r, tmin, tmax, t);
 }
 
 template <class R>
 __device__ __forceinline__ bool hit_object(const SceneDev& s, uint32_t id, V3<R> o, V3<R> d, R tmin, R tmax, R& t) {
-    if (id < (uint32_t)s.S) {
-        V3<R> c;
-        R r;
-        Obj<R>::sphere(s, id, c, r);
-        return hit_sphere(o, d, c, r, tmin, tmax, t);
-    }
-    V3<R> p0, a;
-    R L, r;
-    Obj<R>::cylinder(s, id - (uint32_t)s.S, p0, a, L, r);
-    return hit_cylinder(o, d, p0, a, L, r, tmin, tmax, t);
+    return hit_object<R>(Obj<R>::base(s), id, o, d, tmin, tmax, t);
 }
 
 // ---------------------------------------------------------------- grid walk
@@ -440,22 +423,16 @@ __device__ __forceinline__ int ao_visible(const FrameDev& f, uint32_t q, V3<R> o
 // normal turned to face the incoming ray.
 __device__ __forceinline__ void reproject64(const SceneDev& s, uint32_t id, V3<double> o, V3<double> d, double t,
                                             V3<double>& p, V3<double>& n) {
+    V3<double> p0, a;
+    double L, r;
+    Obj<double>::load(s.obj64, id, p0, a, L, r);
     p = madd(o, t, d);
-    if (id < (uint32_t)s.S) {
-        V3<double> c;
-        double r;
-        Obj<double>::sphere(s, id, c, r);
-        n = normalized(p - c);
-        p = madd(c, r, n);
-    } else {
-        V3<double> p0, a;
-        double L, r;
-        Obj<double>::cylinder(s, id - (uint32_t)s.S, p0, a, L, r);
-        double sa = dot(p - p0, a);
-        V3<double> q = madd(p0, sa, a);
-        n = normalized(p - q);
-        p = madd(q, r, n);
-    }
+    // closest point of the generator (centre, or axis point) to the hit point
+    double sa = dot(p - p0, a);
+    V3<double> q = madd(p0, sa, a);
+    V3<double> v = p - q;
+    n = (1.0 / sqrt(dot(v, v))) * v;
+    p = madd(q, r, n);
     if (dot(n, d) > 0.0) n = v3(-n.x, -n.y, -n.z);
 }
 

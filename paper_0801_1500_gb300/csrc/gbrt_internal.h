@@ -47,11 +47,8 @@ struct Scene {
     int device = 0;
     int64_t S = 0, C = 0;
     int32_t K = 0;
-    float4* sph = nullptr;
-    float4* cyl_a = nullptr;
-    float4* cyl_b = nullptr;
-    double2* sph64 = nullptr;
-    double2* cyl64 = nullptr;
+    float4* obj = nullptr;
+    double2* obj64 = nullptr;
     uint32_t* color = nullptr;
     float* palette = nullptr;
     float4* aabb = nullptr;  // [2 (S + C)]: lo (xyz), hi (xyz) per object
@@ -64,11 +61,8 @@ struct Scene {
         v.C = (int32_t)C;
         v.K = K;
         v.pad = 0;
-        v.sph = sph;
-        v.cyl_a = cyl_a;
-        v.cyl_b = cyl_b;
-        v.sph64 = sph64;
-        v.cyl64 = cyl64;
+        v.obj = obj;
+        v.obj64 = obj64;
         v.color = color;
         v.palette = palette;
         return v;

@@ -16,20 +16,17 @@ enum : uint32_t {
     ERR_QUEUE_TIMEOUT = 4u,  // a bounded wait on the work queue ran out
 };
 
-// Scene in the device layout.
-//   sph    float4 [S]   centre xyz, radius
-//   cyl_a  float4 [C]   end p0 xyz, radius
-//   cyl_b  float4 [C]   unit axis xyz, length
-//   sph64  double2[2S]  (cx, cy), (cz, r)
-//   cyl64  double2[4C]  (p0x, p0y), (p0z, ax), (ay, az), (L, r)
+// Scene in the device layout: one record per object, indexed by global id
+// (spheres 0..S-1, then cylinders S..S+C-1), the same shape for both kinds so
+// a single branch-free test serves both (a sphere is a cylinder record with a
+// zero axis and zero length):
+//   obj    float4 [2 (S+C)]  (p0 xyz, radius), (unit axis xyz, length)
+//   obj64  double2[4 (S+C)]  (p0x, p0y), (p0z, radius), (ax, ay), (az, length)
 //   color  uint32 [S+C] palette index; palette float [K*3]
 struct SceneDev {
     int32_t S, C, K, pad;
-    const float4* sph;
-    const float4* cyl_a;
-    const float4* cyl_b;
-    const double2* sph64;
-    const double2* cyl64;
+    const float4* obj;
+    const double2* obj64;
     const uint32_t* color;
     const float* palette;
 };
@@ -53,6 +50,10 @@ struct FrameDev {
     // camera (double) -- the float path rounds the primary ray from these
     double eye[3], dir[3], up[3], right[3];
     double half_w, half_h;
+    double inv_w, inv_h;  // 1/W, 1/H
+    double dir_unit[3];   // dir / |dir|
+    float dir_f[3], up_f[3], right_f[3];
+    float half_w_f, half_h_f, inv_w_f, inv_h_f;
     int32_t cam_kind;
     int32_t W, H, spp;
     uint32_t frame;

@@ -36,17 +36,30 @@ __device__ __forceinline__ int find_frame(const T* off, int n, T x) {
 }
 
 // Primary ray of pixel (i, j), in FP64 (both paths derive their ray from it).
+// 1/W, 1/H and the unit view direction come precomputed with the frame.
 __device__ __forceinline__ void primary_ray64(const FrameDev& f, int i, int j, V3<double>& o, V3<double>& d) {
-    double u = f.half_w * (2.0 * ((double)i + 0.5) / (double)f.W - 1.0);
-    double v = f.half_h * (1.0 - 2.0 * ((double)j + 0.5) / (double)f.H);
-    V3<double> eye = ld3(f.eye), dir = ld3(f.dir), up = ld3(f.up), right = ld3(f.right);
+    double u = f.half_w * fma((double)(2 * i + 1), f.inv_w, -1.0);
+    double v = f.half_h * fma(-(double)(2 * j + 1), f.inv_h, 1.0);
+    V3<double> up = ld3(f.up), right = ld3(f.right);
     if (f.cam_kind == GBRT_CAMERA_ORTHO) {
-        o = madd(madd(eye, u, right), v, up);
-        d = normalized(dir);
+        o = madd(madd(ld3(f.eye), u, right), v, up);
+        d = ld3(f.dir_unit);
     } else {
-        o = eye;
-        d = normalized(madd(madd(dir, u, right), v, up));
+        o = ld3(f.eye);
+        V3<double> q = madd(madd(ld3(f.dir_unit), u, right), v, up);
+        d = rsqrt(dot(q, q)) * q;
     }
+}
+
+// View direction of pixel q in FP32 (shading only).
+__device__ __forceinline__ V3<float> view_dir_f(const FrameDev& f, uint32_t q) {
+    V3<float> d = v3(f.dir_f[0], f.dir_f[1], f.dir_f[2]);
+    if (f.cam_kind == GBRT_CAMERA_ORTHO) return d;
+    const int i = (int)(q % (uint32_t)f.W), j = (int)(q / (uint32_t)f.W);
+    float u = f.half_w_f * fmaf((float)(2 * i + 1), f.inv_w_f, -1.0f);
+    float v = f.half_h_f * fmaf(-(float)(2 * j + 1), f.inv_h_f, 1.0f);
+    d = madd(madd(d, u, v3(f.right_f[0], f.right_f[1], f.right_f[2])), v, v3(f.up_f[0], f.up_f[1], f.up_f[2]));
+    return rsqrtf(dot(d, d)) * d;
 }
 
 // FP32 path: nearest hit in FP32 from the FP32 ray re-based at the grid entry
@@ -174,9 +187,26 @@ __global__ void __launch_bounds__(256) k_primary(const __grid_constant__ BatchDe
         const uint32_t q = (uint32_t)j * (uint32_t)F.W + (uint32_t)i;
         if (hit) {
             const int64_t slot = F.hit_base + base + __popc(hm & ((1u << lane) - 1u));
-            V3<double> p, n;
-            reproject64(F.scene, id, o64, d64, t64, p, n);
-            HitIO<R>::store(b.hits, slot, madd(p, F.eps, n), n, q, id);
+            V3<double> ao_o, n;
+            if (MODE == GBRT_FP32) {
+                // FP64 hit point and its foot q on the generator (centre or axis);
+                // the unit normal in FP32; AO origin q + (r + eps) n in FP64
+                V3<double> p0, a;
+                double L, r;
+                Obj<double>::load(F.scene.obj64, id, p0, a, L, r);
+                V3<double> p = madd(o64, t64, d64);
+                V3<double> qq = madd(p0, dot(p - p0, a), a);
+                V3<float> nf = to_f(p - qq);
+                nf = rsqrtf(dot(nf, nf)) * nf;
+                if (dot(to_f(d64), nf) > 0.0f) nf = v3(-nf.x, -nf.y, -nf.z);
+                n = to_d(nf);
+                ao_o = madd(qq, r + F.eps, n);
+            } else {
+                V3<double> p;
+                reproject64(F.scene, id, o64, d64, t64, p, n);
+                ao_o = madd(p, F.eps, n);
+            }
+            HitIO<R>::store(b.hits, slot, ao_o, n, q, id);
             b.vis[slot] = 0u;
             if (F.out_ids) F.out_ids[q] = id;
         } else {
@@ -217,25 +247,36 @@ __global__ void k_ao_plan(const __grid_constant__ BatchDev b) {
 
 // ---------------------------------------------------------------- AO pass
 
+// Per-warp shared state of the cooperative AO walk: each lane's ray and the
+// candidate range of its current cell, laid out so the warp can test all
+// (ray, candidate) pairs 32 at a time.
+template <class R>
+struct AoWarp {
+    unsigned excl[32];         // exclusive prefix of candidate counts
+    unsigned first[32];        // first item index of the lane's current cell
+    V3<R> o[32], d[32];
+    R tmax[32];
+    ObjPtr<R> obj[32];
+    const uint32_t* items[32];
+};
+
 template <class R>
 __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDev b) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    AoWarp<R>& S = reinterpret_cast<AoWarp<R>*>(smem_raw)[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     const unsigned long long total = b.job_off[b.nframes];
     const int refill = b.refill;
-    bool has = false, exhausted = false, overflow = false;
-    V3<R> o, d;
-    R tmax = R(0);
+    bool has = false, fresh = false, exhausted = false, overflow = false;
     Walk<R> w;
     uint32_t k = 0, e = 0;
     int64_t vslot = 0;
-    SceneDev sc;
     const uint2* cells = nullptr;
-    const uint32_t* items = nullptr;
     while (true) {
+        // 1. compaction: idle lanes take the next rays together
         const unsigned act = __ballot_sync(FULL, has);
         if (!exhausted && __popc(act) < refill) {
-            // compaction: the idle lanes of the warp take the next rays together
             const unsigned idle = ~act;
             unsigned long long base = 0;
             if (lane == 0) base = atomicAdd(b.queue + 1, (unsigned long long)__popc(idle));
@@ -248,24 +289,28 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
                     const FrameDev& F = b.frames[f];
                     const unsigned long long jl = jj - b.job_off[f];
                     const uint32_t spp = (uint32_t)F.spp;
-                    const uint32_t h = (uint32_t)(jl / spp);
+                    const uint32_t h = jl < 0xFFFFFFFFull ? (uint32_t)jl / spp : (uint32_t)(jl / spp);
                     const uint32_t smp = (uint32_t)(jl - (unsigned long long)h * spp);
                     vslot = F.hit_base + h;
-                    V3<R> n;
+                    V3<R> o, n;
                     uint32_t q, oid;
                     HitIO<R>::load(b.hits, vslot, o, n, q, oid);
                     uint32_t b1, b2;
                     ao_uniforms(q, smp, F.frame, F.seed_lo, F.seed_hi, b1, b2);
-                    d = cosine_dir(n, b1, b2);
-                    tmax = ao_maxdist<R>(F);
+                    const V3<R> d = cosine_dir(n, b1, b2);
+                    const R tmax = ao_maxdist<R>(F);
                     if (walk_start(F.grid, o, d, R(0), tmax, w)) {
-                        sc = F.scene;
                         cells = F.grid.cells;
-                        items = F.grid.items;
+                        S.o[lane] = o;
+                        S.d[lane] = d;
+                        S.tmax[lane] = tmax;
+                        S.obj[lane] = Obj<R>::base(F.scene);
+                        S.items[lane] = F.grid.items;
                         const uint2 cr = __ldg(cells + w.cell);
                         k = cr.x;
                         e = cr.x + cr.y;
                         has = true;
+                        fresh = true;
                     } else {
                         atomicAdd(b.vis + vslot, 1u);  // leaves the grid at once: escapes
                     }
@@ -273,8 +318,8 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
             }
         }
         if (exhausted && __ballot_sync(FULL, has) == 0) break;
-        if (has && k >= e) {
-            // next cell with candidates, or the end of the walk (the ray escapes)
+        // 2. every ray whose cell was tested moves on to its next non-empty cell
+        if (has && !fresh) {
             bool more;
             do {
                 more = walk_next(w, overflow);
@@ -284,16 +329,44 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
                 e = cr.x + cr.y;
             } while (k >= e);
             if (!more) {
-                atomicAdd(b.vis + vslot, 1u);
+                atomicAdd(b.vis + vslot, 1u);  // walked out of the grid: escapes
                 has = false;
             }
         }
-        if (has) {
-            const uint32_t id = __ldg(items + k);
-            ++k;
-            R t;
-            if (hit_object(sc, id, o, d, R(0), tmax, t)) has = false;  // occluded: any hit ends the ray
+        // 3. lay the warp's (ray, candidate) pairs out densely
+        const unsigned cnt = has ? e - k : 0u;
+        unsigned incl = cnt;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            unsigned y = __shfl_up_sync(FULL, incl, off);
+            if (lane >= off) incl += y;
         }
+        const unsigned T = __shfl_sync(FULL, incl, 31);
+        S.excl[lane] = incl - cnt;
+        S.first[lane] = k;
+        __syncwarp();
+        // 4. test them 32 at a time, every lane busy; OR the hits back per ray
+        unsigned hitbits = 0;
+        for (unsigned base = 0; base < T; base += 32) {
+            const unsigned p = base + lane;
+            bool hit = false;
+            unsigned r = 0;
+            if (p < T) {
+#pragma unroll
+                for (unsigned step = 16; step > 0; step >>= 1)
+                    if (S.excl[r + step] <= p) r += step;
+                const uint32_t id = __ldg(S.items[r] + S.first[r] + (p - S.excl[r]));
+                R t;
+                hit = hit_object<R>(S.obj[r], id, S.o[r], S.d[r], R(0), S.tmax[r], t);
+            }
+            hitbits |= __reduce_or_sync(FULL, hit ? (1u << r) : 0u);
+        }
+        // 5. any hit occludes the ray; otherwise its cell is done
+        if (has) {
+            if ((hitbits >> lane) & 1u) has = false;
+            else fresh = false;
+        }
+        __syncwarp();
     }
     if (overflow) atomicOr(b.err, ERR_DDA_STEPS);
 }
@@ -312,11 +385,17 @@ __global__ void __launch_bounds__(256) k_shade(const __grid_constant__ BatchDev 
         uint32_t q, id;
         HitIO<R>::load(b.hits, slot, o, n, q, id);
         const uint32_t vis = b.vis[slot];
-        V3<double> o64, d64;
-        primary_ray64(F, (int)(q % (uint32_t)F.W), (int)(q / (uint32_t)F.W), o64, d64);
+        V3<R> d;
+        if (std::is_same<R, float>::value) {
+            V3<float> df = view_dir_f(F, q);
+            d = v3((R)df.x, (R)df.y, (R)df.z);
+        } else {
+            V3<double> o64, d64;
+            primary_ray64(F, (int)(q % (uint32_t)F.W), (int)(q / (uint32_t)F.W), o64, d64);
+            d = v3((R)d64.x, (R)d64.y, (R)d64.z);
+        }
         R V = F.spp > 0 ? (R)vis / (R)F.spp : R(1);
         R rgb[3];
-        V3<R> d = v3((R)d64.x, (R)d64.y, (R)d64.z);
         shade<R>(F, id, n, d, V, rgb);
         R* out = (R*)F.out_rgb + 3 * (size_t)q;
         out[0] = rgb[0];
@@ -374,9 +453,9 @@ int grow(Ctx* ctx, void** p, size_t* cap, size_t need) {
 }
 
 template <class K>
-int persistent_grid(Ctx* ctx, K kernel, int block) {
+int persistent_grid(Ctx* ctx, K kernel, int block, size_t smem = 0) {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, 0) != cudaSuccess || per_sm < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem) != cudaSuccess || per_sm < 1)
         per_sm = 1;
     if (ctx->tuning.ctas_per_sm > 0) per_sm = std::min(per_sm, ctx->tuning.ctas_per_sm);
     return per_sm * ctx->num_sms;
@@ -395,10 +474,10 @@ static Grids grids_for(Ctx* ctx, int precision) {
     Grids g;
     if (precision == GBRT_FP32) {
         g.primary = persistent_grid(ctx, k_primary<GBRT_FP32>, block);
-        g.ao = persistent_grid(ctx, k_ao_walk<float>, block);
+        g.ao = persistent_grid(ctx, k_ao_walk<float>, block, (block / 32) * sizeof(AoWarp<float>));
     } else {
         g.primary = persistent_grid(ctx, k_primary<GBRT_FP64>, block);
-        g.ao = persistent_grid(ctx, k_ao_walk<double>, block);
+        g.ao = persistent_grid(ctx, k_ao_walk<double>, block, (block / 32) * sizeof(AoWarp<double>));
     }
     g.shade = ctx->num_sms * 8;
     return g;
@@ -413,12 +492,12 @@ static int enqueue_batch(Ctx* ctx, cudaStream_t stream, int precision, const Bat
     if (precision == GBRT_FP32) {
         k_primary<GBRT_FP32><<<gr.primary, block, 0, stream>>>(bd);
         k_ao_plan<<<1, 32, 0, stream>>>(bd);
-        k_ao_walk<float><<<gr.ao, block, 0, stream>>>(bd);
+        k_ao_walk<float><<<gr.ao, block, (block / 32) * sizeof(AoWarp<float>), stream>>>(bd);
         k_shade<float><<<gr.shade, 256, 0, stream>>>(bd);
     } else {
         k_primary<GBRT_FP64><<<gr.primary, block, 0, stream>>>(bd);
         k_ao_plan<<<1, 32, 0, stream>>>(bd);
-        k_ao_walk<double><<<gr.ao, block, 0, stream>>>(bd);
+        k_ao_walk<double><<<gr.ao, block, (block / 32) * sizeof(AoWarp<double>), stream>>>(bd);
         k_shade<double><<<gr.shade, 256, 0, stream>>>(bd);
     }
     ctx->launches += 4;

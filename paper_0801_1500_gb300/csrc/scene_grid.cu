@@ -28,9 +28,8 @@ static float float_of_ord(uint32_t o) {
 // warp-reduced scene box. box[0..2] min, box[3..5] max (ordered), box[6] = 1
 // when any object is invalid.
 __global__ void __launch_bounds__(256) k_scene_prep(const float* sph_in, int64_t S, const float* cyl_in, int64_t C,
-                                                     const uint32_t* color, int32_t K, float4* sph, float4* cyl_a,
-                                                     float4* cyl_b, double2* sph64, double2* cyl64, float4* aabb,
-                                                     uint32_t* box) {
+                                                     const uint32_t* color, int32_t K, float4* obj, double2* obj64,
+                                                     float4* aabb, uint32_t* box) {
     const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const float big = 3.0e38f;
     float lo[3] = {big, big, big}, hi[3] = {-big, -big, -big};
@@ -39,9 +38,12 @@ __global__ void __launch_bounds__(256) k_scene_prep(const float* sph_in, int64_t
         const float* p = sph_in + 4 * id;
         float c[3] = {p[0], p[1], p[2]}, r = p[3];
         bad = !(isfinite(c[0]) && isfinite(c[1]) && isfinite(c[2]) && isfinite(r) && r > 0.0f);
-        sph[id] = make_float4(c[0], c[1], c[2], r);
-        sph64[2 * id] = make_double2(c[0], c[1]);
-        sph64[2 * id + 1] = make_double2(c[2], r);
+        obj[2 * id] = make_float4(c[0], c[1], c[2], r);
+        obj[2 * id + 1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        obj64[4 * id] = make_double2(c[0], c[1]);
+        obj64[4 * id + 1] = make_double2(c[2], r);
+        obj64[4 * id + 2] = make_double2(0.0, 0.0);
+        obj64[4 * id + 3] = make_double2(0.0, 0.0);
         for (int k = 0; k < 3; ++k) {
             lo[k] = c[k] - r;
             hi[k] = c[k] + r;
@@ -65,12 +67,12 @@ __global__ void __launch_bounds__(256) k_scene_prep(const float* sph_in, int64_t
             a[k] = L > 0.0f ? ax[k] / L : 0.0f;
             a64[k] = L64 > 0.0 ? ax64[k] / L64 : 0.0;
         }
-        cyl_a[j] = make_float4(p0[0], p0[1], p0[2], r);
-        cyl_b[j] = make_float4(a[0], a[1], a[2], L);
-        cyl64[4 * j] = make_double2(p0[0], p0[1]);
-        cyl64[4 * j + 1] = make_double2(p0[2], a64[0]);
-        cyl64[4 * j + 2] = make_double2(a64[1], a64[2]);
-        cyl64[4 * j + 3] = make_double2(L64, r);
+        obj[2 * id] = make_float4(p0[0], p0[1], p0[2], r);
+        obj[2 * id + 1] = make_float4(a[0], a[1], a[2], L);
+        obj64[4 * id] = make_double2(p0[0], p0[1]);
+        obj64[4 * id + 1] = make_double2(p0[2], r);
+        obj64[4 * id + 2] = make_double2(a64[0], a64[1]);
+        obj64[4 * id + 3] = make_double2(a64[2], L64);
         for (int k = 0; k < 3; ++k) {
             float e = r * sqrtf(fmaxf(0.0f, 1.0f - a[k] * a[k]));
             lo[k] = fminf(p0[k], p1[k]) - e;
@@ -275,11 +277,8 @@ static bool host_scene_valid(const float* sph, int64_t S, const float* cyl, int6
 }
 
 void scene_release(Scene* s) {
-    cudaFree(s->sph);
-    cudaFree(s->cyl_a);
-    cudaFree(s->cyl_b);
-    cudaFree(s->sph64);
-    cudaFree(s->cyl64);
+    cudaFree(s->obj);
+    cudaFree(s->obj64);
     cudaFree(s->color);
     cudaFree(s->palette);
     cudaFree(s->aabb);
@@ -302,19 +301,15 @@ int scene_upload(Ctx* ctx, const float* spheres, int64_t S, const float* cyl, in
     s->C = C;
     s->K = K;
     {
-        const size_t nS = (size_t)std::max<int64_t>(S, 1), nC = (size_t)std::max<int64_t>(C, 1),
-                     nN = (size_t)std::max<int64_t>(N, 1);
-        GB_TRY(cudaMalloc(&s->sph, nS * sizeof(float4)));
-        GB_TRY(cudaMalloc(&s->cyl_a, nC * sizeof(float4)));
-        GB_TRY(cudaMalloc(&s->cyl_b, nC * sizeof(float4)));
-        GB_TRY(cudaMalloc(&s->sph64, 2 * nS * sizeof(double2)));
-        GB_TRY(cudaMalloc(&s->cyl64, 4 * nC * sizeof(double2)));
+        const size_t nN = (size_t)std::max<int64_t>(N, 1);
+        GB_TRY(cudaMalloc(&s->obj, 2 * nN * sizeof(float4)));
+        GB_TRY(cudaMalloc(&s->obj64, 4 * nN * sizeof(double2)));
         GB_TRY(cudaMalloc(&s->color, nN * sizeof(uint32_t)));
         GB_TRY(cudaMalloc(&s->palette, (size_t)std::max(K, 1) * 3 * sizeof(float)));
         GB_TRY(cudaMalloc(&s->aabb, 2 * nN * sizeof(float4)));
         GB_TRY(cudaMalloc(&d_box, 8 * sizeof(uint32_t)));
-        s->bytes = nS * (sizeof(float4) + 2 * sizeof(double2)) + nC * (2 * sizeof(float4) + 4 * sizeof(double2)) +
-                   nN * (sizeof(uint32_t) + 2 * sizeof(float4)) + (size_t)std::max(K, 1) * 3 * sizeof(float);
+        s->bytes = nN * (2 * sizeof(float4) + 4 * sizeof(double2) + sizeof(uint32_t) + 2 * sizeof(float4)) +
+                   (size_t)std::max(K, 1) * 3 * sizeof(float);
         if (host) {
             if (S > 0) {
                 GB_TRY(cudaMalloc(&d_sph_in, (size_t)S * 4 * sizeof(float)));
@@ -353,8 +348,8 @@ int scene_upload(Ctx* ctx, const float* spheres, int64_t S, const float* cyl, in
         GB_TRY(cudaMemcpyAsync(d_box, init, sizeof(init), cudaMemcpyHostToDevice, ctx->stream));
         if (N > 0) {
             int blocks = (int)((N + 255) / 256);
-            k_scene_prep<<<blocks, 256, 0, ctx->stream>>>(d_sph_in, S, d_cyl_in, C, s->color, K, s->sph, s->cyl_a,
-                                                          s->cyl_b, s->sph64, s->cyl64, s->aabb, d_box);
+            k_scene_prep<<<blocks, 256, 0, ctx->stream>>>(d_sph_in, S, d_cyl_in, C, s->color, K, s->obj, s->obj64,
+                                                          s->aabb, d_box);
             ctx->launches++;
             GB_TRY(cudaGetLastError());
         }
