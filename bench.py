@@ -229,6 +229,9 @@ def main():
     ap.add_argument("--workload", default="paper_1mp")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--lam", type=float, default=2.0)
+    ap.add_argument("--refill", type=int, default=0, help="AO lane refill threshold (0 = library default)")
+    ap.add_argument("--block", type=int, default=0, help="threads per CTA of the persistent kernels")
+    ap.add_argument("--tile", default="", help="primary tile WxH, product 32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-budget", type=float, default=8.0)
     args = ap.parse_args()
@@ -251,6 +254,14 @@ def main():
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
     r = G.Renderer(local, stream)
+    tun = G.gbrt_get_tuning(r.ctx)
+    if args.refill:
+        tun["refill"] = args.refill
+    if args.block:
+        tun["block"] = args.block
+    if args.tile:
+        tun["tile_w"], tun["tile_h"] = (int(x) for x in args.tile.split("x"))
+    G.gbrt_set_tuning(r.ctx, **tun)
     scene, grid = r.upload(w.scene, lam=args.lam)
     W, H, p = w.width, w.height, w.params
     spp = p.ao_samples
@@ -365,6 +376,7 @@ def main():
             "data": "synthetic",
             "config": {"workload": w.name, "width": W, "height": H, "ao_samples": spp,
                        "objects": w.scene.n_objects, "precision": args.precision, "grid_lambda": args.lam,
+                       "tuning": G.gbrt_get_tuning(r.ctx),
                        "rays_per_frame": rays_per_frame, "hit_pixels": hits,
                        "l2": "flushed between steps (512 MB write outside the timed events)"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),

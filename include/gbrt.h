@@ -150,7 +150,7 @@ typedef struct gbrt_render_item {
  *  tile_w x tile_h  pixels of one primary-ray work item (a warp); the product
  *                   must be 32
  *  block            threads per CTA of the persistent kernels (multiple of
- *                   32, <= 1024)
+ *                   32, <= 256)
  *  ctas_per_sm      resident CTAs per SM of the persistent launches (0 = as
  *                   many as fit)
  *  refill           AO lanes: a warp refills its idle lanes with new shadow

@@ -433,7 +433,7 @@ GBRT_API int gbrt_philox4x32_10(gbrt_ctx* ctx, const uint32_t* ctr, const uint32
 GBRT_API int gbrt_set_tuning(gbrt_ctx* ctx, const gbrt_tuning* t) {
     if (!ctx || !t) return GBRT_EINVAL;
     if (t->tile_w <= 0 || t->tile_h <= 0 || t->tile_w * t->tile_h != 32) return GBRT_EINVAL;
-    if (t->block < 32 || t->block > 1024 || t->block % 32 != 0) return GBRT_EINVAL;
+    if (t->block < 32 || t->block > 256 || t->block % 32 != 0) return GBRT_EINVAL;
     if (t->ctas_per_sm < 0 || t->ctas_per_sm > 32) return GBRT_EINVAL;
     if (t->refill < 1 || t->refill > 32) return GBRT_EINVAL;
     ctx->tuning = *t;

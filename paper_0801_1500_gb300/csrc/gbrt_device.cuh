@@ -156,6 +156,8 @@ struct GridP;
 
 template <>
 struct GridP<float> {
+    static __device__ __forceinline__ float bs(const GridDev& g, int k) { return g.bs[k]; }
+    static __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
     static __device__ __forceinline__ float lo(const GridDev& g, int k) { return g.lo[k]; }
     static __device__ __forceinline__ float hi(const GridDev& g, int k) { return g.hi[k]; }
     static __device__ __forceinline__ float h(const GridDev& g, int k) { return g.h[k]; }
@@ -164,34 +166,59 @@ struct GridP<float> {
 
 template <>
 struct GridP<double> {
+    static __device__ __forceinline__ double bs(const GridDev& g, int k) { return g.bs64[k]; }
+    static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
     static __device__ __forceinline__ double lo(const GridDev& g, int k) { return g.lo64[k]; }
     static __device__ __forceinline__ double hi(const GridDev& g, int k) { return g.hi64[k]; }
     static __device__ __forceinline__ double h(const GridDev& g, int k) { return g.h64[k]; }
     static __device__ __forceinline__ double inv_h(const GridDev& g, int k) { return g.inv_h64[k]; }
 };
 
-// Clip o + t d, t in [tmin, tmax], to the grid box.
+// Clip o + t d, t in [tmin, tmax], to the grid box and to the bounding sphere
+// of the objects (nothing can be hit outside either). inv = 1/d per axis
+// (unused where d is 0).
 template <class R>
-__device__ __forceinline__ bool clip_grid(const GridDev& g, V3<R> o, V3<R> d, R tmin, R tmax, R& t0, R& t1) {
+__device__ __forceinline__ bool clip_grid(const GridDev& g, V3<R> o, V3<R> d, V3<R> inv, R tmin, R tmax, R& t0,
+                                          R& t1) {
     R a = tmin, b = tmax;
     const R oo[3] = {o.x, o.y, o.z};
     const R dd[3] = {d.x, d.y, d.z};
+    const R ii[3] = {inv.x, inv.y, inv.z};
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         R lo = GridP<R>::lo(g, k), hi = GridP<R>::hi(g, k);
         if (dd[k] == R(0)) {
             if (oo[k] < lo || oo[k] > hi) return false;
         } else {
-            R inv = R(1) / dd[k];
-            R ta = (lo - oo[k]) * inv, tb = (hi - oo[k]) * inv;
+            R ta = (lo - oo[k]) * ii[k], tb = (hi - oo[k]) * ii[k];
             R mn = ta < tb ? ta : tb, mx = ta < tb ? tb : ta;
             a = mn > a ? mn : a;
             b = mx < b ? mx : b;
         }
     }
+    // bounding sphere: |o + t d - c| <= rb (|d| = 1)
+    V3<R> f = v3(o.x - GridP<R>::bs(g, 0), o.y - GridP<R>::bs(g, 1), o.z - GridP<R>::bs(g, 2));
+    R bb = dot(f, d);
+    V3<R> v = madd(f, -bb, d);
+    R rb = GridP<R>::bs(g, 3);
+    R disc = rb * rb - dot(v, v);
+    if (disc < R(0)) return false;
+    R sq = Num<R>::sqrt_(disc);
+    a = (-bb - sq) > a ? (-bb - sq) : a;
+    b = (-bb + sq) < b ? (-bb + sq) : b;
     t0 = a;
     t1 = b;
     return a <= b;
+}
+
+template <class R>
+__device__ __forceinline__ V3<R> inv_dir(V3<R> d) {
+    return v3(GridP<R>::rcp(d.x), GridP<R>::rcp(d.y), GridP<R>::rcp(d.z));
+}
+
+template <class R>
+__device__ __forceinline__ bool clip_grid(const GridDev& g, V3<R> o, V3<R> d, R tmin, R tmax, R& t0, R& t1) {
+    return clip_grid(g, o, d, inv_dir(d), tmin, tmax, t0, t1);
 }
 
 // Amanatides & Woo (1987) traversal state: current cell, per-axis step, the t
@@ -209,16 +236,14 @@ struct Walk {
 };
 
 template <class R>
-__device__ __forceinline__ void axis_setup(const GridDev& g, int k, R o, R d, int c, int& s, R& tn, R& td) {
+__device__ __forceinline__ void axis_setup(const GridDev& g, int k, R o, R d, R inv, int c, int& s, R& tn, R& td) {
     R inf = Num<R>::inf();
     if (d > R(0)) {
         s = 1;
-        R inv = R(1) / d;
         tn = (GridP<R>::lo(g, k) + R(c + 1) * GridP<R>::h(g, k) - o) * inv;
         td = GridP<R>::h(g, k) * inv;
     } else if (d < R(0)) {
         s = -1;
-        R inv = R(1) / d;
         tn = (GridP<R>::lo(g, k) + R(c) * GridP<R>::h(g, k) - o) * inv;
         td = -GridP<R>::h(g, k) * inv;
     } else {
@@ -239,14 +264,15 @@ __device__ __forceinline__ int cell_of(const GridDev& g, int k, R x) {
 template <class R>
 __device__ __forceinline__ bool walk_start(const GridDev& g, V3<R> o, V3<R> d, R tmin, R tmax, Walk<R>& w) {
     R t0, t1;
-    if (g.empty || !clip_grid(g, o, d, tmin, tmax, t0, t1)) return false;
+    const V3<R> inv = inv_dir(d);
+    if (g.empty || !clip_grid(g, o, d, inv, tmin, tmax, t0, t1)) return false;
     V3<R> p = madd(o, t0, d);
     w.cx = cell_of(g, 0, p.x);
     w.cy = cell_of(g, 1, p.y);
     w.cz = cell_of(g, 2, p.z);
-    axis_setup(g, 0, o.x, d.x, w.cx, w.sx, w.tnx, w.tdx);
-    axis_setup(g, 1, o.y, d.y, w.cy, w.sy, w.tny, w.tdy);
-    axis_setup(g, 2, o.z, d.z, w.cz, w.sz, w.tnz, w.tdz);
+    axis_setup(g, 0, o.x, d.x, inv.x, w.cx, w.sx, w.tnx, w.tdx);
+    axis_setup(g, 1, o.y, d.y, inv.y, w.cy, w.sy, w.tny, w.tdy);
+    axis_setup(g, 2, o.z, d.z, inv.z, w.cz, w.sz, w.tnz, w.tdz);
     w.t1 = t1;
     w.nx = g.n[0];
     w.ny = g.n[1];
@@ -421,7 +447,7 @@ __device__ __forceinline__ int ao_visible(const FrameDev& f, uint32_t q, V3<R> o
 
 // FP64 hit point re-projected onto the surface of object id, and the geometric
 // normal turned to face the incoming ray.
-__device__ __forceinline__ void reproject64(const SceneDev& s, uint32_t id, V3<double> o, V3<double> d, double t,
+__device__ __forceinline__ bool reproject64(const SceneDev& s, uint32_t id, V3<double> o, V3<double> d, double t,
                                             V3<double>& p, V3<double>& n) {
     V3<double> p0, a;
     double L, r;
@@ -433,7 +459,12 @@ __device__ __forceinline__ void reproject64(const SceneDev& s, uint32_t id, V3<d
     V3<double> v = p - q;
     n = (1.0 / sqrt(dot(v, v))) * v;
     p = madd(q, r, n);
-    if (dot(n, d) > 0.0) n = v3(-n.x, -n.y, -n.z);
+    // true when the ray met the surface from inside (the normal is turned)
+    if (dot(n, d) > 0.0) {
+        n = v3(-n.x, -n.y, -n.z);
+        return true;
+    }
+    return false;
 }
 
 // ---------------------------------------------------------------- shading

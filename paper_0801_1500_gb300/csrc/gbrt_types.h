@@ -36,6 +36,10 @@ struct SceneDev {
 struct GridDev {
     float lo[3], hi[3], h[3], inv_h[3];
     double lo64[3], hi64[3], h64[3], inv_h64[3];
+    // bounding sphere of all objects (centre xyz, radius): walks are clipped to
+    // it, so rays skip the empty corners of the grid box
+    float bs[4];
+    double bs64[4];
     int32_t n[3];
     int32_t empty;
     int64_t ncells;

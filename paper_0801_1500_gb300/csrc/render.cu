@@ -89,7 +89,10 @@ __device__ __forceinline__ bool nearest_fp32_refined(const FrameDev& f, V3<doubl
     return true;
 }
 
-// Hit records: (AO origin xyz, pixel) and (normal xyz, object id).
+// Hit records: (AO origin xyz, pixel) and (normal xyz, object id). Bit 31 of
+// the pixel word marks a hit from inside the surface (its normal turned
+// toward the axis or centre); pixel indices stay below 2^31.
+constexpr uint32_t HIT_INSIDE = 0x80000000u;
 template <class R>
 struct HitIO;
 
@@ -188,6 +191,7 @@ __global__ void __launch_bounds__(256) k_primary(const __grid_constant__ BatchDe
         if (hit) {
             const int64_t slot = F.hit_base + base + __popc(hm & ((1u << lane) - 1u));
             V3<double> ao_o, n;
+            bool inside_hit = false;
             if (MODE == GBRT_FP32) {
                 // FP64 hit point and its foot q on the generator (centre or axis);
                 // the unit normal in FP32; AO origin q + (r + eps) n in FP64
@@ -198,15 +202,18 @@ __global__ void __launch_bounds__(256) k_primary(const __grid_constant__ BatchDe
                 V3<double> qq = madd(p0, dot(p - p0, a), a);
                 V3<float> nf = to_f(p - qq);
                 nf = rsqrtf(dot(nf, nf)) * nf;
-                if (dot(to_f(d64), nf) > 0.0f) nf = v3(-nf.x, -nf.y, -nf.z);
+                if (dot(to_f(d64), nf) > 0.0f) {
+                    nf = v3(-nf.x, -nf.y, -nf.z);
+                    inside_hit = true;
+                }
                 n = to_d(nf);
                 ao_o = madd(qq, r + F.eps, n);
             } else {
                 V3<double> p;
-                reproject64(F.scene, id, o64, d64, t64, p, n);
+                inside_hit = reproject64(F.scene, id, o64, d64, t64, p, n);
                 ao_o = madd(p, F.eps, n);
             }
-            HitIO<R>::store(b.hits, slot, ao_o, n, q, id);
+            HitIO<R>::store(b.hits, slot, ao_o, n, q | (inside_hit ? HIT_INSIDE : 0u), id);
             b.vis[slot] = 0u;
             if (F.out_ids) F.out_ids[q] = id;
         } else {
@@ -247,17 +254,22 @@ __global__ void k_ao_plan(const __grid_constant__ BatchDev b) {
 
 // ---------------------------------------------------------------- AO pass
 
-// Per-warp shared state of the cooperative AO walk: each lane's ray and the
-// candidate range of its current cell, laid out so the warp can test all
-// (ray, candidate) pairs 32 at a time.
+// Per-warp shared state of the cooperative AO walk.
+//   list[lane][*]  the lane's candidates of its current cell after filtering
+//                  (rows padded to 17 words: distinct rays fall in distinct banks)
+//   mbox[slot][lane]  ids this ray has already tested, direct-mapped by id
+//                  (a re-test of a missed object cannot hit: skipping it is exact)
+constexpr int AO_CAP = 16;
+constexpr int AO_MBOX = 16;
+
 template <class R>
 struct AoWarp {
-    unsigned excl[32];         // exclusive prefix of candidate counts
-    unsigned first[32];        // first item index of the lane's current cell
+    unsigned excl[32];
+    uint32_t list[32][AO_CAP + 1];
+    uint32_t mbox[AO_MBOX][32];
     V3<R> o[32], d[32];
     R tmax[32];
     ObjPtr<R> obj[32];
-    const uint32_t* items[32];
 };
 
 template <class R>
@@ -268,11 +280,12 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
     const unsigned lt = (1u << lane) - 1u;
     const unsigned long long total = b.job_off[b.nframes];
     const int refill = b.refill;
-    bool has = false, fresh = false, exhausted = false, overflow = false;
+    bool has = false, exhausted = false, overflow = false;
     Walk<R> w;
-    uint32_t k = 0, e = 0;
+    uint32_t k = 0, e = 0, self = GBRT_MISS;
     int64_t vslot = 0;
     const uint2* cells = nullptr;
+    const uint32_t* items = nullptr;
     while (true) {
         // 1. compaction: idle lanes take the next rays together
         const unsigned act = __ballot_sync(FULL, has);
@@ -293,33 +306,37 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
                     const uint32_t smp = (uint32_t)(jl - (unsigned long long)h * spp);
                     vslot = F.hit_base + h;
                     V3<R> o, n;
-                    uint32_t q, oid;
-                    HitIO<R>::load(b.hits, vslot, o, n, q, oid);
+                    uint32_t q;
+                    HitIO<R>::load(b.hits, vslot, o, n, q, self);
+                    // the own object can be skipped only behind a convex outer side
+                    if (q & HIT_INSIDE) self = GBRT_MISS;
+                    q &= ~HIT_INSIDE;
                     uint32_t b1, b2;
                     ao_uniforms(q, smp, F.frame, F.seed_lo, F.seed_hi, b1, b2);
                     const V3<R> d = cosine_dir(n, b1, b2);
                     const R tmax = ao_maxdist<R>(F);
                     if (walk_start(F.grid, o, d, R(0), tmax, w)) {
                         cells = F.grid.cells;
+                        items = F.grid.items;
                         S.o[lane] = o;
                         S.d[lane] = d;
                         S.tmax[lane] = tmax;
                         S.obj[lane] = Obj<R>::base(F.scene);
-                        S.items[lane] = F.grid.items;
+#pragma unroll
+                        for (int m = 0; m < AO_MBOX; ++m) S.mbox[m][lane] = GBRT_MISS;
                         const uint2 cr = __ldg(cells + w.cell);
                         k = cr.x;
                         e = cr.x + cr.y;
                         has = true;
-                        fresh = true;
                     } else {
-                        atomicAdd(b.vis + vslot, 1u);  // leaves the grid at once: escapes
+                        atomicAdd(b.vis + vslot, 1u);  // misses the objects' bounds: escapes
                     }
                 }
             }
         }
         if (exhausted && __ballot_sync(FULL, has) == 0) break;
-        // 2. every ray whose cell was tested moves on to its next non-empty cell
-        if (has && !fresh) {
+        // 2. rays whose cell is exhausted move on to the next non-empty cell
+        if (has && k >= e) {
             bool more;
             do {
                 more = walk_next(w, overflow);
@@ -329,12 +346,25 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
                 e = cr.x + cr.y;
             } while (k >= e);
             if (!more) {
-                atomicAdd(b.vis + vslot, 1u);  // walked out of the grid: escapes
+                atomicAdd(b.vis + vslot, 1u);  // walked out: escapes
                 has = false;
             }
         }
-        // 3. lay the warp's (ray, candidate) pairs out densely
-        const unsigned cnt = has ? e - k : 0u;
+        // 3. each lane stages its cell's candidates, minus its own object (an AO
+        //    ray leaving a convex surface outward cannot meet it again) and
+        //    objects it already tested in an earlier cell
+        unsigned cnt = 0;
+        if (has) {
+            while (k < e && cnt < AO_CAP) {
+                const uint32_t id = __ldg(items + k);
+                ++k;
+                if (id == self) continue;
+                const uint32_t m = id & (AO_MBOX - 1);
+                if (S.mbox[m][lane] == id) continue;
+                S.mbox[m][lane] = id;
+                S.list[lane][cnt++] = id;
+            }
+        }
         unsigned incl = cnt;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
@@ -343,9 +373,8 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
         }
         const unsigned T = __shfl_sync(FULL, incl, 31);
         S.excl[lane] = incl - cnt;
-        S.first[lane] = k;
         __syncwarp();
-        // 4. test them 32 at a time, every lane busy; OR the hits back per ray
+        // 4. test all (ray, candidate) pairs 32 at a time; OR the hits per ray
         unsigned hitbits = 0;
         for (unsigned base = 0; base < T; base += 32) {
             const unsigned p = base + lane;
@@ -355,17 +384,14 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
 #pragma unroll
                 for (unsigned step = 16; step > 0; step >>= 1)
                     if (S.excl[r + step] <= p) r += step;
-                const uint32_t id = __ldg(S.items[r] + S.first[r] + (p - S.excl[r]));
+                const uint32_t id = S.list[r][p - S.excl[r]];
                 R t;
                 hit = hit_object<R>(S.obj[r], id, S.o[r], S.d[r], R(0), S.tmax[r], t);
             }
             hitbits |= __reduce_or_sync(FULL, hit ? (1u << r) : 0u);
         }
-        // 5. any hit occludes the ray; otherwise its cell is done
-        if (has) {
-            if ((hitbits >> lane) & 1u) has = false;
-            else fresh = false;
-        }
+        // 5. any hit occludes the ray
+        if (has && ((hitbits >> lane) & 1u)) has = false;
         __syncwarp();
     }
     if (overflow) atomicOr(b.err, ERR_DDA_STEPS);
@@ -384,6 +410,7 @@ __global__ void __launch_bounds__(256) k_shade(const __grid_constant__ BatchDev 
         V3<R> o, n;
         uint32_t q, id;
         HitIO<R>::load(b.hits, slot, o, n, q, id);
+        q &= ~HIT_INSIDE;
         const uint32_t vis = b.vis[slot];
         V3<R> d;
         if (std::is_same<R, float>::value) {

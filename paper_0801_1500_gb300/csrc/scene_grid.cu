@@ -153,6 +153,25 @@ __global__ void __launch_bounds__(256) k_grid_scatter(const float4* aabb, int64_
             }
 }
 
+// Radius of the sphere about `ctr` that holds every object: sphere |c - ctr| + r,
+// cylinder max over both ends of |p - ctr| + r (FP64, rounded up to float).
+__global__ void __launch_bounds__(256) k_bound_radius(const double2* obj64, int64_t N, double cx, double cy,
+                                                       double cz, unsigned int* rbits) {
+    int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float rr = 0.0f;
+    if (id < N) {
+        const double2* q = obj64 + 4 * id;
+        double2 q0 = q[0], q1 = q[1], q2 = q[2], q3 = q[3];
+        double px = q0.x - cx, py = q0.y - cy, pz = q1.x - cz;
+        double r = q1.y, L = q3.y;
+        double ex = px + L * q2.x, ey = py + L * q2.y, ez = pz + L * q3.x;
+        double d = fmax(sqrt(px * px + py * py + pz * pz), sqrt(ex * ex + ey * ey + ez * ez)) + r;
+        rr = __double2float_ru(d);
+    }
+    for (int off = 16; off > 0; off >>= 1) rr = fmaxf(rr, __shfl_xor_sync(0xffffffffu, rr, off));
+    if ((threadIdx.x & 31) == 0) atomicMax(rbits, __float_as_uint(rr));  // non-negative floats order as ints
+}
+
 // Atomic scatter order is arbitrary: sort each cell's ids ascending (spheres
 // first, then cylinders; deterministic lists).
 __global__ void __launch_bounds__(256) k_cell_sort(const uint2* cells, int64_t ncells, uint32_t* items) {
@@ -441,14 +460,38 @@ int grid_build(Ctx* ctx, const Scene* s, float lambda, Grid* g) {
             GB_TRY(cudaGetLastError());
         }
         const int64_t nb = (nc + SCAN_TILE - 1) / SCAN_TILE;
-        GB_TRY(cudaMalloc(&sums, (size_t)(nb + 1) * sizeof(unsigned long long)));
+        GB_TRY(cudaMalloc(&sums, (size_t)(nb + 2) * sizeof(unsigned long long)));
+        // bounding sphere about the box centre
+        const double ctr[3] = {0.5 * ((double)d.lo[0] + d.hi[0]), 0.5 * ((double)d.lo[1] + d.hi[1]),
+                               0.5 * ((double)d.lo[2] + d.hi[2])};
+        unsigned int* rbits = (unsigned int*)(sums + nb + 1);
+        GB_TRY(cudaMemsetAsync(rbits, 0, sizeof(unsigned long long), ctx->stream));
+        if (N > 0) {
+            k_bound_radius<<<(int)((N + 255) / 256), 256, 0, ctx->stream>>>(s->obj64, N, ctr[0], ctr[1], ctr[2], rbits);
+            ctx->launches++;
+        }
         k_scan_reduce<<<(int)nb, SCAN_T, 0, ctx->stream>>>(counts, nc, sums);
         k_scan_sums<<<1, SCAN_T, 0, ctx->stream>>>(sums, nb, sums + nb);
         k_scan_apply<<<(int)nb, SCAN_T, 0, ctx->stream>>>(counts, nc, sums, g->cells);
         ctx->launches += 3;
         GB_TRY(cudaGetLastError());
-        GB_TRY(cudaMemcpyAsync(&h_total, sums + nb, sizeof(h_total), cudaMemcpyDeviceToHost, ctx->stream));
+        unsigned long long h_tail[2] = {0, 0};
+        GB_TRY(cudaMemcpyAsync(h_tail, sums + nb, sizeof(h_tail), cudaMemcpyDeviceToHost, ctx->stream));
         GB_TRY(cudaStreamSynchronize(ctx->stream));
+        h_total = h_tail[0];
+        {
+            float rb;
+            unsigned int bits = (unsigned int)(h_tail[1] & 0xFFFFFFFFull);
+            memcpy(&rb, &bits, 4);
+            double rpad = (double)rb * (1.0 + 1e-5) + (double)pad;
+            for (int k = 0; k < 3; ++k) {
+                d.bs64[k] = ctr[k];
+                d.bs[k] = (float)ctr[k];
+            }
+            d.bs64[3] = rpad;
+            // the float copy: pad for the rounding of the float centre too
+            d.bs[3] = (float)(rpad + 1e-6 * (fabs(ctr[0]) + fabs(ctr[1]) + fabs(ctr[2]) + 1.0));
+        }
         if (h_total >= 0xFFFFFFFFull) {
             rc = GBRT_ENOMEM;
             goto fail;

@@ -246,3 +246,37 @@ def test_deterministic_and_grid_invariant(G, R):
     for f in frames[1:]:
         assert (f[1] != frames[0][1]).mean() < 1e-3
         assert (np.abs(f[0] - frames[0][0]).max(axis=1) > 1 / 255).mean() < 2e-3
+
+
+@pytest.mark.parametrize("prec", [S.PRECISION_FP32, S.PRECISION_FP64])
+def test_open_tube_inner_wall(G, R, oracle, prec):
+    # seen obliquely, an open tube shows its inner wall through the end, whose AO
+    # rays meet the opposite wall of the same tube
+    sc = S.make_scene(None, [[-3, -1, 0, 3, 1, 0.5, 0.7]])
+    W, H = 64, 40
+    cam = S.ortho_camera(sc, W, H, angle_deg=70.0)
+    p = S.Params(ao_samples=16, seed=4, precision=prec)
+    scene, grid = R.upload(sc)
+    rgb, ids, vis = gpu_frame(G, R, scene, grid, cam, W, H, S.default_lights(), p)
+    ref = oracle.render(sc, cam, W, H, S.default_lights(), p, mode="brute")
+    hit = ref["id"] != oracle.MISS
+    assert (ref["vis"][hit] < 16).sum() > 20  # the case under test occurs
+    st = compare(rgb, ids, vis, ref)
+    assert st["id_mismatch"] == 0 and st["vis_eq"] >= 0.995, st
+    R.free(scene, grid)
+
+
+@pytest.mark.parametrize("prec", [S.PRECISION_FP32, S.PRECISION_FP64])
+def test_pinhole_camera_inside_an_atom(G, R, oracle, prec):
+    sc = S.globule(400, 380, 12.0, seed=6)
+    c = sc.spheres[17, :3].astype(np.float64)
+    cam = S.Camera(eye=tuple(c), dir=(0.0, 0.0, -1.0), up=(0.0, 1.0, 0.0), right=(1.0, 0.0, 0.0),
+                   half_w=0.8, half_h=0.6, kind=S.CAMERA_PINHOLE)
+    W, H = 48, 36
+    p = S.Params(ao_samples=8, seed=9, precision=prec)
+    scene, grid = R.upload(sc, lam=2.0)
+    rgb, ids, vis = gpu_frame(G, R, scene, grid, cam, W, H, S.default_lights(), p)
+    ref = oracle.render(sc, cam, W, H, S.default_lights(), p, mode="brute")
+    st = compare(rgb, ids, vis, ref)
+    assert st["id_mismatch"] == 0 and st["frac_bad"] <= 1.0 / (W * H), st
+    R.free(scene, grid)
