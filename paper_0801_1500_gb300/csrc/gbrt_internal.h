@@ -13,6 +13,7 @@ namespace gbrt {
 struct Ctx {
     int device = 0;
     int num_sms = 1;
+    bool smem_configured = false;
     cudaStream_t stream = nullptr;
     uint32_t* d_err = nullptr;   // device error word (ERR_* bits)
     uint32_t* h_err = nullptr;   // pinned mirror

@@ -498,6 +498,14 @@ struct Grids {
 
 static Grids grids_for(Ctx* ctx, int precision) {
     const int block = ctx->tuning.block;
+    if (!ctx->smem_configured) {
+        // the AO kernels' per-warp staging can exceed the 48 KB default
+        cudaFuncSetAttribute(k_ao_walk<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(8 * sizeof(AoWarp<float>)));
+        cudaFuncSetAttribute(k_ao_walk<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(8 * sizeof(AoWarp<double>)));
+        ctx->smem_configured = true;
+    }
     Grids g;
     if (precision == GBRT_FP32) {
         g.primary = persistent_grid(ctx, k_primary<GBRT_FP32>, block);
