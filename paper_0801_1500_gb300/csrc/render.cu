@@ -194,7 +194,8 @@ __global__ void __launch_bounds__(256) k_primary(const __grid_constant__ BatchDe
             bool inside_hit = false;
             if (MODE == GBRT_FP32) {
                 // FP64 hit point and its foot q on the generator (centre or axis);
-                // the unit normal in FP32; AO origin q + (r + eps) n in FP64
+                // the outward unit normal in FP32; the surface point q + r n_out
+                // and the AO origin one eps along the normal facing the ray
                 V3<double> p0, a;
                 double L, r;
                 Obj<double>::load(F.scene.obj64, id, p0, a, L, r);
@@ -202,12 +203,14 @@ __global__ void __launch_bounds__(256) k_primary(const __grid_constant__ BatchDe
                 V3<double> qq = madd(p0, dot(p - p0, a), a);
                 V3<float> nf = to_f(p - qq);
                 nf = rsqrtf(dot(nf, nf)) * nf;
+                const V3<double> n_out = to_d(nf);
+                const V3<double> ps = madd(qq, r, n_out);
                 if (dot(to_f(d64), nf) > 0.0f) {
                     nf = v3(-nf.x, -nf.y, -nf.z);
                     inside_hit = true;
                 }
                 n = to_d(nf);
-                ao_o = madd(qq, r + F.eps, n);
+                ao_o = madd(ps, F.eps, n);
             } else {
                 V3<double> p;
                 inside_hit = reproject64(F.scene, id, o64, d64, t64, p, n);
