@@ -257,24 +257,27 @@ __global__ void k_ao_plan(const __grid_constant__ BatchDev b) {
 
 // ---------------------------------------------------------------- AO pass
 
-// Per-warp shared state of the cooperative AO walk.
-//   list[lane][*]  the lane's candidates of its current cell after filtering
-//                  (rows padded to 17 words: distinct rays fall in distinct banks)
-//   mbox[slot][lane]  ids this ray has already tested, direct-mapped by id
-//                  (a re-test of a missed object cannot hit: skipping it is exact)
-constexpr int AO_CAP = 16;
+// Per-warp shared state of the cooperative AO walk: each lane's ray and the
+// item range of its current cell, and per ray a direct-mapped mailbox of ids
+// it has already tested (a re-test of a missed object cannot hit, so skipping
+// it is exact). mbox[slot][lane]: each lane's slots sit in its own bank.
 constexpr int AO_MBOX = 16;
 
 template <class R>
 struct AoWarp {
     unsigned excl[32];
-    uint32_t list[32][AO_CAP + 1];
+    unsigned first[32];
+    uint32_t self[32];
     uint32_t mbox[AO_MBOX][32];
     V3<R> o[32], d[32];
     R tmax[32];
     ObjPtr<R> obj[32];
+    const uint32_t* items[32];
 };
 
+// Lockstep cooperative walk: every iteration each active ray advances one cell
+// (all lanes run the same step code); the warp then lays the (ray, item) pairs
+// of those cells out densely with a scan and tests them 32 at a time.
 template <class R>
 __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDev b) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -283,12 +286,11 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
     const unsigned lt = (1u << lane) - 1u;
     const unsigned long long total = b.job_off[b.nframes];
     const int refill = b.refill;
-    bool has = false, exhausted = false, overflow = false;
+    bool has = false, fresh = false, exhausted = false, overflow = false;
     Walk<R> w;
-    uint32_t k = 0, e = 0, self = GBRT_MISS;
+    uint32_t k = 0, e = 0;
     int64_t vslot = 0;
     const uint2* cells = nullptr;
-    const uint32_t* items = nullptr;
     while (true) {
         // 1. compaction: idle lanes take the next rays together
         const unsigned act = __ballot_sync(FULL, has);
@@ -309,7 +311,7 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
                     const uint32_t smp = (uint32_t)(jl - (unsigned long long)h * spp);
                     vslot = F.hit_base + h;
                     V3<R> o, n;
-                    uint32_t q;
+                    uint32_t q, self;
                     HitIO<R>::load(b.hits, vslot, o, n, q, self);
                     // the own object can be skipped only behind a convex outer side
                     if (q & HIT_INSIDE) self = GBRT_MISS;
@@ -320,17 +322,19 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
                     const R tmax = ao_maxdist<R>(F);
                     if (walk_start(F.grid, o, d, R(0), tmax, w)) {
                         cells = F.grid.cells;
-                        items = F.grid.items;
                         S.o[lane] = o;
                         S.d[lane] = d;
                         S.tmax[lane] = tmax;
                         S.obj[lane] = Obj<R>::base(F.scene);
+                        S.items[lane] = F.grid.items;
+                        S.self[lane] = self;
 #pragma unroll
                         for (int m = 0; m < AO_MBOX; ++m) S.mbox[m][lane] = GBRT_MISS;
                         const uint2 cr = __ldg(cells + w.cell);
                         k = cr.x;
                         e = cr.x + cr.y;
                         has = true;
+                        fresh = true;
                     } else {
                         atomicAdd(b.vis + vslot, 1u);  // misses the objects' bounds: escapes
                     }
@@ -338,36 +342,20 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
             }
         }
         if (exhausted && __ballot_sync(FULL, has) == 0) break;
-        // 2. rays whose cell is exhausted move on to the next non-empty cell
-        if (has && k >= e) {
-            bool more;
-            do {
-                more = walk_next(w, overflow);
-                if (!more) break;
+        // 2. every other active ray steps one cell
+        if (has && !fresh) {
+            if (walk_next(w, overflow)) {
                 const uint2 cr = __ldg(cells + w.cell);
                 k = cr.x;
                 e = cr.x + cr.y;
-            } while (k >= e);
-            if (!more) {
+            } else {
                 atomicAdd(b.vis + vslot, 1u);  // walked out: escapes
                 has = false;
             }
         }
-        // 3. each lane stages its cell's candidates, minus its own object (an AO
-        //    ray leaving a convex surface outward cannot meet it again) and
-        //    objects it already tested in an earlier cell
-        unsigned cnt = 0;
-        if (has) {
-            while (k < e && cnt < AO_CAP) {
-                const uint32_t id = __ldg(items + k);
-                ++k;
-                if (id == self) continue;
-                const uint32_t m = id & (AO_MBOX - 1);
-                if (S.mbox[m][lane] == id) continue;
-                S.mbox[m][lane] = id;
-                S.list[lane][cnt++] = id;
-            }
-        }
+        fresh = false;
+        // 3. lay the warp's (ray, item) pairs out densely
+        const unsigned cnt = has ? e - k : 0u;
         unsigned incl = cnt;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
@@ -375,23 +363,31 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
             if (lane >= off) incl += y;
         }
         const unsigned T = __shfl_sync(FULL, incl, 31);
-        S.excl[lane] = incl - cnt;
-        __syncwarp();
-        // 4. test all (ray, candidate) pairs 32 at a time; OR the hits per ray
         unsigned hitbits = 0;
-        for (unsigned base = 0; base < T; base += 32) {
-            const unsigned p = base + lane;
-            bool hit = false;
-            unsigned r = 0;
-            if (p < T) {
+        if (T > 0) {
+            S.excl[lane] = incl - cnt;
+            S.first[lane] = k;
+            __syncwarp();
+            // 4. test the pairs 32 at a time (own object and re-tests skipped);
+            //    OR the hits back per ray
+            for (unsigned base = 0; base < T; base += 32) {
+                const unsigned p = base + lane;
+                bool hit = false;
+                unsigned r = 0;
+                if (p < T) {
 #pragma unroll
-                for (unsigned step = 16; step > 0; step >>= 1)
-                    if (S.excl[r + step] <= p) r += step;
-                const uint32_t id = S.list[r][p - S.excl[r]];
-                R t;
-                hit = hit_object<R>(S.obj[r], id, S.o[r], S.d[r], R(0), S.tmax[r], t);
+                    for (unsigned step = 16; step > 0; step >>= 1)
+                        if (S.excl[r + step] <= p) r += step;
+                    const uint32_t id = __ldg(S.items[r] + S.first[r] + (p - S.excl[r]));
+                    const uint32_t m = id & (AO_MBOX - 1);
+                    if (id != S.self[r] && S.mbox[m][r] != id) {
+                        S.mbox[m][r] = id;
+                        R t;
+                        hit = hit_object<R>(S.obj[r], id, S.o[r], S.d[r], R(0), S.tmax[r], t);
+                    }
+                }
+                hitbits |= __reduce_or_sync(FULL, hit ? (1u << r) : 0u);
             }
-            hitbits |= __reduce_or_sync(FULL, hit ? (1u << r) : 0u);
         }
         // 5. any hit occludes the ray
         if (has && ((hitbits >> lane) & 1u)) has = false;
