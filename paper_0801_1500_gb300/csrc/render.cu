@@ -257,27 +257,56 @@ __global__ void k_ao_plan(const __grid_constant__ BatchDev b) {
 
 // ---------------------------------------------------------------- AO pass
 
-// Per-warp shared state of the cooperative AO walk: each lane's ray and the
-// item range of its current cell, and per ray a direct-mapped mailbox of ids
-// it has already tested (a re-test of a missed object cannot hit, so skipping
-// it is exact). mbox[slot][lane]: each lane's slots sit in its own bank.
+// Ray record in shared memory: (origin, tmax) and (direction, -) -- two
+// 128-bit loads per test in the FP32 path.
+template <class R>
+struct __align__(16) AoRay {
+    V3<R> o;
+    R tmax;
+    V3<R> d;
+    R pad;
+};
+
+// Per-warp shared state of the cooperative AO walk.
+//   excl/first   the scan of the lanes' candidate counts and their first items
+//   mbox[lane]   direct-mapped ids this ray already tested (rows padded to 17
+//                words so distinct rays and slots fall in distinct banks); a
+//                re-test of a missed object cannot hit, so skipping it is exact
+//   qr/qid       surviving (ray, object) pairs waiting for a full test batch
 constexpr int AO_MBOX = 16;
 
 template <class R>
 struct AoWarp {
+    AoRay<R> ray[32];
     unsigned excl[32];
     unsigned first[32];
     uint32_t self[32];
-    uint32_t mbox[AO_MBOX][32];
-    V3<R> o[32], d[32];
-    R tmax[32];
+    uint32_t mbox[32][AO_MBOX + 1];
     ObjPtr<R> obj[32];
     const uint32_t* items[32];
+    uint32_t qid[64];
+    uint8_t qr[64];
 };
 
+// Test queued pairs [0, n) (n <= 32), one per lane; returns the rays hit, as bits.
+template <class R>
+__device__ __forceinline__ unsigned ao_test_batch(AoWarp<R>& S, int lane, unsigned n) {
+    bool hit = false;
+    unsigned r = 0;
+    if ((unsigned)lane < n) {
+        r = S.qr[lane];
+        const uint32_t id = S.qid[lane];
+        const AoRay<R> ray = S.ray[r];
+        R t;
+        hit = hit_object<R>(S.obj[r], id, ray.o, ray.d, R(0), ray.tmax, t);
+    }
+    return __reduce_or_sync(FULL, hit ? (1u << r) : 0u);
+}
+
 // Lockstep cooperative walk: every iteration each active ray advances one cell
-// (all lanes run the same step code); the warp then lays the (ray, item) pairs
-// of those cells out densely with a scan and tests them 32 at a time.
+// (all lanes run the same step code); the warp lays the (ray, item) pairs of
+// those cells out densely with a scan, drops the ray's own object and
+// re-tests, compacts the survivors and tests them in full batches of 32.
 template <class R>
 __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDev b) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -292,7 +321,7 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
     int64_t vslot = 0;
     const uint2* cells = nullptr;
     while (true) {
-        // 1. compaction: idle lanes take the next rays together
+        // 1. compaction of rays: idle lanes take the next rays together
         const unsigned act = __ballot_sync(FULL, has);
         if (!exhausted && __popc(act) < refill) {
             const unsigned idle = ~act;
@@ -322,14 +351,17 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
                     const R tmax = ao_maxdist<R>(F);
                     if (walk_start(F.grid, o, d, R(0), tmax, w)) {
                         cells = F.grid.cells;
-                        S.o[lane] = o;
-                        S.d[lane] = d;
-                        S.tmax[lane] = tmax;
+                        AoRay<R> ray;
+                        ray.o = o;
+                        ray.tmax = tmax;
+                        ray.d = d;
+                        ray.pad = R(0);
+                        S.ray[lane] = ray;
                         S.obj[lane] = Obj<R>::base(F.scene);
                         S.items[lane] = F.grid.items;
                         S.self[lane] = self;
 #pragma unroll
-                        for (int m = 0; m < AO_MBOX; ++m) S.mbox[m][lane] = GBRT_MISS;
+                        for (int m = 0; m < AO_MBOX; ++m) S.mbox[lane][m] = GBRT_MISS;
                         const uint2 cr = __ldg(cells + w.cell);
                         k = cr.x;
                         e = cr.x + cr.y;
@@ -368,25 +400,45 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
             S.excl[lane] = incl - cnt;
             S.first[lane] = k;
             __syncwarp();
-            // 4. test the pairs 32 at a time (own object and re-tests skipped);
-            //    OR the hits back per ray
+            // 4. map pairs to (ray, object), drop the own object and re-tests,
+            //    queue the survivors; test whenever 32 are queued
+            unsigned qn = 0;
             for (unsigned base = 0; base < T; base += 32) {
                 const unsigned p = base + lane;
-                bool hit = false;
+                bool keep = false;
                 unsigned r = 0;
+                uint32_t id = 0;
                 if (p < T) {
 #pragma unroll
                     for (unsigned step = 16; step > 0; step >>= 1)
                         if (S.excl[r + step] <= p) r += step;
-                    const uint32_t id = __ldg(S.items[r] + S.first[r] + (p - S.excl[r]));
-                    const uint32_t m = id & (AO_MBOX - 1);
-                    if (id != S.self[r] && S.mbox[m][r] != id) {
-                        S.mbox[m][r] = id;
-                        R t;
-                        hit = hit_object<R>(S.obj[r], id, S.o[r], S.d[r], R(0), S.tmax[r], t);
-                    }
+                    id = __ldg(S.items[r] + S.first[r] + (p - S.excl[r]));
+                    uint32_t* slot = &S.mbox[r][id & (AO_MBOX - 1)];
+                    keep = id != S.self[r] && *slot != id;
+                    if (keep) *slot = id;
                 }
-                hitbits |= __reduce_or_sync(FULL, hit ? (1u << r) : 0u);
+                const unsigned bal = __ballot_sync(FULL, keep);
+                if (keep) {
+                    const unsigned pos = qn + __popc(bal & lt);
+                    S.qr[pos] = (uint8_t)r;
+                    S.qid[pos] = id;
+                }
+                qn += __popc(bal);
+                if (qn >= 32) {
+                    __syncwarp();
+                    hitbits |= ao_test_batch(S, lane, 32u);
+                    __syncwarp();
+                    if ((unsigned)lane < qn - 32) {
+                        S.qr[lane] = S.qr[32 + lane];
+                        S.qid[lane] = S.qid[32 + lane];
+                    }
+                    qn -= 32;
+                    __syncwarp();
+                }
+            }
+            if (qn > 0) {
+                __syncwarp();
+                hitbits |= ao_test_batch(S, lane, qn);
             }
         }
         // 5. any hit occludes the ray
