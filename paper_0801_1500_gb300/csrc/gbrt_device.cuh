@@ -423,10 +423,10 @@ __device__ __forceinline__ V3<R> cosine_dir(V3<R> n, uint32_t b1, uint32_t b2) {
     R b = n.x * n.y * a;
     V3<R> e1 = v3(R(1) + sign * n.x * n.x * a, sign * b, -sign * n.x);
     V3<R> e2 = v3(b, sign + n.y * n.y * a, -n.y);
-    R r = Num<R>::sqrt_(u1);
+    R r = sqrt_pos(u1);
     R sp, cp;
     sincos_2pi<R>(u2, sp, cp);
-    R x = r * cp, y = r * sp, z = Num<R>::sqrt_(R(1) - u1);
+    R x = r * cp, y = r * sp, z = sqrt_pos(R(1) - u1);
     return v3(x * e1.x + y * e2.x + z * n.x, x * e1.y + y * e2.y + z * n.y, x * e1.z + y * e2.z + z * n.z);
 }
 

@@ -278,28 +278,27 @@ constexpr int AO_MBOX = 16;
 template <class R>
 struct AoWarp {
     AoRay<R> ray[32];
-    unsigned excl[32];
-    unsigned first[32];
+    unsigned delta[32];  // item index of pair p of ray r: p + delta[r]
     uint32_t self[32];
+    uint32_t owner[32];  // ray whose pairs start at this position of the current chunk
     uint32_t mbox[32][AO_MBOX + 1];
     ObjPtr<R> obj[32];
     const uint32_t* items[32];
     uint32_t qid[64];
-    uint8_t qr[64];
+    uint32_t qr[64];
 };
 
-// Test queued pairs [0, n) (n <= 32), one per lane; returns the rays hit, as bits.
+// Test queued pairs [0, n) (1 <= n <= 32), one per lane (lanes past n redo
+// pair 0 and discard it, so the batch runs without branches); returns the
+// rays hit, as bits.
 template <class R>
 __device__ __forceinline__ unsigned ao_test_batch(AoWarp<R>& S, int lane, unsigned n) {
-    bool hit = false;
-    unsigned r = 0;
-    if ((unsigned)lane < n) {
-        r = S.qr[lane];
-        const uint32_t id = S.qid[lane];
-        const AoRay<R> ray = S.ray[r];
-        R t;
-        hit = hit_object<R>(S.obj[r], id, ray.o, ray.d, R(0), ray.tmax, t);
-    }
+    const unsigned idx = (unsigned)lane < n ? (unsigned)lane : 0u;
+    const unsigned r = S.qr[idx];
+    const uint32_t id = S.qid[idx];
+    const AoRay<R> ray = S.ray[r];
+    R t;
+    const bool hit = hit_object<R>(S.obj[r], id, ray.o, ray.d, R(0), ray.tmax, t) && (unsigned)lane < n;
     return __reduce_or_sync(FULL, hit ? (1u << r) : 0u);
 }
 
@@ -397,35 +396,35 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
         const unsigned T = __shfl_sync(FULL, incl, 31);
         unsigned hitbits = 0;
         if (T > 0) {
-            S.excl[lane] = incl - cnt;
-            S.first[lane] = k;
-            __syncwarp();
+            const unsigned ex = incl - cnt;
+            S.delta[lane] = k - ex;
             // 4. map pairs to (ray, object), drop the own object and re-tests,
             //    queue the survivors; test whenever 32 are queued
             unsigned qn = 0;
             for (unsigned base = 0; base < T; base += 32) {
-                const unsigned p = base + lane;
-                bool keep = false;
-                unsigned r = 0;
-                uint32_t id = 0;
-                if (p < T) {
-#pragma unroll
-                    for (unsigned step = 16; step > 0; step >>= 1)
-                        if (S.excl[r + step] <= p) r += step;
-                    id = __ldg(S.items[r] + S.first[r] + (p - S.excl[r]));
-                    uint32_t* slot = &S.mbox[r][id & (AO_MBOX - 1)];
-                    keep = id != S.self[r] && *slot != id;
-                    if (keep) *slot = id;
-                }
+                // rays mark where their pairs start inside this chunk; a pair's
+                // ray is the last start at or before it
+                const bool mine = cnt > 0 && ex < base + 32 && ex + cnt > base;
+                const unsigned pos = ex > base ? ex - base : 0u;
+                if (mine) S.owner[pos] = (uint32_t)lane;
+                const unsigned starts = __reduce_or_sync(FULL, mine ? (1u << pos) : 0u);
+                __syncwarp();
+                const unsigned p = base + lane < T ? base + lane : T - 1u;
+                const unsigned r = S.owner[31 - __clz(starts & (0xFFFFFFFFu >> (31 - lane)))];
+                const uint32_t id = __ldg(S.items[r] + (p + S.delta[r]));
+                uint32_t* slot = &S.mbox[r][id & (AO_MBOX - 1)];
+                const uint32_t seen = *slot;
+                const bool keep = base + lane < T && id != S.self[r] && seen != id;
                 const unsigned bal = __ballot_sync(FULL, keep);
                 if (keep) {
-                    const unsigned pos = qn + __popc(bal & lt);
-                    S.qr[pos] = (uint8_t)r;
-                    S.qid[pos] = id;
+                    *slot = id;
+                    const unsigned q = qn + __popc(bal & lt);
+                    S.qr[q] = r;
+                    S.qid[q] = id;
                 }
                 qn += __popc(bal);
+                __syncwarp();
                 if (qn >= 32) {
-                    __syncwarp();
                     hitbits |= ao_test_batch(S, lane, 32u);
                     __syncwarp();
                     if ((unsigned)lane < qn - 32) {
@@ -436,10 +435,7 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
                     __syncwarp();
                 }
             }
-            if (qn > 0) {
-                __syncwarp();
-                hitbits |= ao_test_batch(S, lane, qn);
-            }
+            if (qn > 0) hitbits |= ao_test_batch(S, lane, qn);
         }
         // 5. any hit occludes the ray
         if (has && ((hitbits >> lane) & 1u)) has = false;
