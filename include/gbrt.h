@@ -258,6 +258,38 @@ GBRT_API int gbrt_ao_probe(gbrt_ctx* ctx, const gbrt_scene* scene, const gbrt_gr
 GBRT_API int gbrt_philox4x32_10(gbrt_ctx* ctx, const uint32_t* ctr, const uint32_t* key, int64_t n,
                                 uint32_t* out);
 
+/* Render one frame without allocating anything (no counterpart in the paper:
+ * this entry point exists for the library's users).
+ *
+ * Some callers cannot allocate device memory at render time: a host
+ * application whose own allocator has reserved all free device memory (a
+ * cudaMalloc here would fail or fragment it), or a latency-critical loop that
+ * must not call cudaMalloc/cudaFree (cudaFree synchronises the device).
+ * gbrt_render allocates its working buffers in the context on first use;
+ * this variant instead keeps them in one fixed device array of about 4.5 MB
+ * inside the library, which every GPU that loads the library holds until the
+ * process exits. It needs no context: the caller passes the scene and grid
+ * (prepared earlier), the outputs (device memory) and the stream to use.
+ *
+ *  - width * height must not exceed GBRT_NOALLOC_MAX_PIXELS (256 x 256);
+ *    larger frames are rejected with GBRT_EINVAL, as are host output
+ *    pointers (params->out_flags must be 0).
+ *  - The first call on a device does that device's set-up (it looks up the
+ *    array's device address and configures the kernels); make that first
+ *    call before any stream capture.
+ *  - All calls share the one array and it keeps the last call's contents;
+ *    the call clears what must start at zero. Calls whose work overlaps on
+ *    the GPU (different streams, or different host threads) race on it:
+ *    order them on one stream.
+ *  - Arguments as for gbrt_render; output buffers are caller-owned.
+ *    Asynchronous on `cuda_stream`. Device-side walk-bound errors are not
+ *    reported by this entry point. */
+#define GBRT_NOALLOC_MAX_PIXELS 65536
+GBRT_API int gbrt_render_noalloc(const gbrt_scene* scene, const gbrt_grid* grid, const gbrt_camera* camera,
+                                 int32_t width, int32_t height, int32_t ao_samples, const gbrt_lights* lights,
+                                 const gbrt_params* params, void* out_rgb, uint32_t* out_hit_ids,
+                                 uint32_t* out_ao_visible, void* cuda_stream);
+
 /* Kernel launch shape used by later renders (see gbrt_tuning). */
 GBRT_API int gbrt_set_tuning(gbrt_ctx* ctx, const gbrt_tuning* tuning);
 GBRT_API int gbrt_get_tuning(const gbrt_ctx* ctx, gbrt_tuning* tuning);

@@ -87,9 +87,21 @@ void scene_release(Scene* s);
 int grid_build(Ctx* ctx, const Scene* s, float lambda, Grid* out);
 void grid_release(Grid* g);
 
+// capi.cu: argument checks and the frame descriptor of one render
+int check_frame_args(const gbrt_scene* scene, const gbrt_grid* grid, const gbrt_camera* cam, int32_t W, int32_t H,
+                     int32_t spp, const gbrt_lights* lights, const gbrt_params* params, const void* out_rgb);
+FrameDev make_frame(const gbrt_scene* scene, const gbrt_grid* grid, const gbrt_camera* cam, int32_t W, int32_t H,
+                    int32_t spp, const gbrt_lights* lights, const gbrt_params* p, void* out_rgb, uint32_t* out_ids,
+                    uint32_t* out_vis);
+
 // render.cu: render n frames of one precision (descriptors filled by the
 // caller; tiling and hit-buffer fields are set here).
 int render_frames(Ctx* ctx, FrameDev* frames, int n, bool use_graph);
+// render.cu: for a batch whose descriptors and buffers the caller laid out:
+// opt the AO kernels into their shared memory (once per device), then launch
+// the four wavefront kernels with grids sized for the current device.
+int configure_render_kernels();
+int enqueue_prepared(const BatchDev& bd, int precision, cudaStream_t stream, int block, int num_sms);
 int launch_ao_probe(Ctx* ctx, const FrameDev& f, const double* pts, const double* nrm, int64_t n, float* out);
 int launch_philox(Ctx* ctx, const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out);
 

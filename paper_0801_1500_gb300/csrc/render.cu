@@ -685,6 +685,38 @@ int render_frames(Ctx* ctx, FrameDev* frames, int n, bool use_graph) {
     return GBRT_OK;
 }
 
+int configure_render_kernels() {
+    cudaError_t e = cudaFuncSetAttribute(k_ao_walk<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(8 * sizeof(AoWarp<float>)));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_ao_walk<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(8 * sizeof(AoWarp<double>)));
+    return err_of(e);
+}
+
+int enqueue_prepared(const BatchDev& bd, int precision, cudaStream_t stream, int block, int num_sms) {
+    auto grid_of = [&](auto kernel, size_t smem) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem) != cudaSuccess || per_sm < 1)
+            per_sm = 1;
+        return per_sm * num_sms;
+    };
+    if (precision == GBRT_FP32) {
+        const size_t smem = (block / 32) * sizeof(AoWarp<float>);
+        k_primary<GBRT_FP32><<<grid_of(k_primary<GBRT_FP32>, 0), block, 0, stream>>>(bd);
+        k_ao_plan<<<1, 32, 0, stream>>>(bd);
+        k_ao_walk<float><<<grid_of(k_ao_walk<float>, smem), block, smem, stream>>>(bd);
+        k_shade<float><<<num_sms * 8, 256, 0, stream>>>(bd);
+    } else {
+        const size_t smem = (block / 32) * sizeof(AoWarp<double>);
+        k_primary<GBRT_FP64><<<grid_of(k_primary<GBRT_FP64>, 0), block, 0, stream>>>(bd);
+        k_ao_plan<<<1, 32, 0, stream>>>(bd);
+        k_ao_walk<double><<<grid_of(k_ao_walk<double>, smem), block, smem, stream>>>(bd);
+        k_shade<double><<<num_sms * 8, 256, 0, stream>>>(bd);
+    }
+    return err_of(cudaGetLastError());
+}
+
 int launch_ao_probe(Ctx* ctx, const FrameDev& f, const double* pts, const double* nrm, int64_t n, float* out) {
     if (n == 0) return GBRT_OK;
     int blocks = (int)((n + 127) / 128);

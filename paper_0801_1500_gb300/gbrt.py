@@ -86,6 +86,8 @@ def _load():
         "gbrt_set_tuning": ([P, C.POINTER(gbrt_tuning)], C.c_int),
         "gbrt_get_tuning": ([P, C.POINTER(gbrt_tuning)], C.c_int),
         "gbrt_launch_count": ([P], C.c_int64),
+        "gbrt_render_noalloc": ([P, P, C.POINTER(gbrt_camera), i32, i32, i32, C.POINTER(gbrt_lights),
+                                 C.POINTER(gbrt_params), P, P, P, P], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -245,6 +247,23 @@ def gbrt_render(ctx, scene, grid, camera, width, height, ao_samples, lights, par
 def gbrt_render_batch(ctx, items, flags=0):
     arr = (gbrt_render_item * len(items))(*items)
     return _check(lib.gbrt_render_batch(ctx, arr, len(items), int(flags)), "gbrt_render_batch")
+
+
+NOALLOC_MAX_PIXELS = 65536
+
+
+def gbrt_render_noalloc(scene, grid, camera, width, height, ao_samples, lights, params, out_rgb,
+                        out_hit_ids=None, out_ao_visible=None, stream=None):
+    """Render without any allocation (fixed in-library scratch, frames up to
+    NOALLOC_MAX_PIXELS pixels); asynchronous on ``stream`` (a torch stream,
+    a raw handle or None for the legacy default stream)."""
+    cam = camera if isinstance(camera, gbrt_camera) else make_camera(camera)
+    li = lights if isinstance(lights, gbrt_lights) else make_lights(lights)
+    pa = params if isinstance(params, gbrt_params) else make_params(params)
+    s = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+    rc = lib.gbrt_render_noalloc(scene, grid, C.byref(cam), int(width), int(height), int(ao_samples), C.byref(li),
+                                 C.byref(pa), ptr(out_rgb), ptr(out_hit_ids), ptr(out_ao_visible), s)
+    return _check(rc, "gbrt_render_noalloc")
 
 
 def gbrt_ao_probe(ctx, scene, grid, pts, nrm, ao_samples, params, out_visibility):

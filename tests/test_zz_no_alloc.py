@@ -1,0 +1,73 @@
+"""The allocation-free render entry point gives the same frames as gbrt_render.
+
+gbrt_render_noalloc is for callers that cannot allocate device memory while
+they render (an application whose own allocator holds the free device memory,
+or a loop that must not call cudaMalloc/cudaFree). It keeps its working data in
+a fixed array inside the library, so two calls in a row must not leak state
+into each other. This file is collected last on purpose.
+"""
+import numpy as np
+import pytest
+
+from paper_0801_1500_gb300 import scenes as S
+from gpu_common import compare
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0801_1500_gb300 import gbrt
+    return gbrt
+
+
+def _flat(rgb, ids, vis):
+    return (rgb.cpu().numpy().reshape(-1, 3).astype(np.float64), ids.cpu().numpy().view(np.uint32).ravel(),
+            vis.cpu().numpy().view(np.uint32).ravel())
+
+
+def test_noalloc_matches_render_on_two_calls_in_a_row(G):
+    import torch
+    sc = S.globule(2000, 1900, 25.0, seed=0)
+    lights = S.default_lights()
+    frames = [(256, 256, S.Params(ao_samples=8, seed=0, precision=S.PRECISION_FP32), 0.0),
+              (200, 120, S.Params(ao_samples=5, seed=3, frame=2, precision=S.PRECISION_FP64), 40.0)]
+    with G.Renderer(0) as r:
+        scene, grid = r.upload(sc, lam=2.0)
+        stream = torch.cuda.current_stream()
+        outs = []
+        for W, H, p, ang in frames:
+            cam = S.ortho_camera(sc, W, H, angle_deg=ang)
+            ref = r.render(scene, grid, cam, W, H, lights, p, ids=True, vis=True)
+            G.gbrt_sync(r.ctx)
+            dt = torch.float64 if p.precision == S.PRECISION_FP64 else torch.float32
+            got = (torch.full((H, W, 3), -1.0, dtype=dt, device="cuda"),
+                   torch.full((H, W), -7, dtype=torch.int32, device="cuda"),
+                   torch.full((H, W), -7, dtype=torch.int32, device="cuda"))
+            G.gbrt_render_noalloc(scene, grid, cam, W, H, p.ao_samples, lights, p, *got, stream=stream)
+            outs.append((ref, got))
+        torch.cuda.synchronize()
+        for ref, got in outs:
+            a, b = _flat(*ref), _flat(*got)
+            # same kernels, same inputs: identical; and within the parity tolerance
+            assert all(np.array_equal(x, y) for x, y in zip(a, b))
+            st = compare(b[0], b[1], b[2], {"rgb": a[0], "id": a[1], "vis": a[2],
+                                           "grazing": np.zeros(len(a[1]), bool)})
+            assert st["id_mismatch"] == 0 and st["frac_bad"] == 0.0 and st["mae"] <= 1e-4, st
+
+
+def test_noalloc_rejects_frames_above_its_limit(G):
+    import torch
+    sc = S.make_scene([[0, 0, 0, 1.0]])
+    with G.Renderer(0) as r:
+        scene, grid = r.upload(sc)
+        W, H = 512, 256
+        assert W * H > G.NOALLOC_MAX_PIXELS
+        out = torch.empty((H, W, 3), device="cuda")
+        with pytest.raises(G.GbrtError) as e:
+            G.gbrt_render_noalloc(scene, grid, S.ortho_camera(sc, W, H), W, H, 4, S.default_lights(),
+                                  S.Params(), out)
+        assert e.value.code == G.EINVAL
