@@ -74,9 +74,9 @@ def sources_hash():
 
 
 def committed_traffic(workload_name, precision):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources (else None)."""
-    p = os.path.join(ROOT, "profiles", f"render_{precision}_{workload_name}.txt")
+    """DRAM bytes per launch of the AO walk kernel from the committed ncu
+    summary, if it was taken on the current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", f"k_ao_walk_{precision}_{workload_name}.txt")
     if not os.path.exists(p):
         return None
     kv = {}
@@ -184,12 +184,13 @@ def oracle_sample(w, lam, budget_s=15.0, threads=0):
                 cores=oracle.max_threads() if threads <= 0 else threads)
 
 
-def per_ray_work(c):
-    """Algorithmic FP32 flops and bytes per ray from the oracle's walk counters."""
-    rays = max(1, c["primary_rays"] + c["ao_rays"])
-    cells = c["primary_cells"] + c["ao_cells"]
-    sph = c["primary_sphere_tests"] + c["ao_sphere_tests"]
-    cyl = c["primary_cylinder_tests"] + c["ao_cylinder_tests"]
+def per_ray_work(c, kind="ao"):
+    """Algorithmic FP32 flops and walk bytes per ray (of one kind: "ao" or
+    "primary") from the oracle's grid-walk counters."""
+    rays = max(1, c[f"{kind}_rays"])
+    cells = c[f"{kind}_cells"]
+    sph = c[f"{kind}_sphere_tests"]
+    cyl = c[f"{kind}_cylinder_tests"]
     flops = (cells * FLOPS_CELL + sph * FLOPS_SPHERE + cyl * FLOPS_CYLINDER) / rays
     nbytes = (cells * BYTES_CELL + (sph + cyl) * BYTES_ITEM + sph * BYTES_SPHERE + cyl * BYTES_CYLINDER) / rays
     return flops, nbytes
@@ -291,6 +292,8 @@ def main():
 
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    phases = []
+    G.gbrt_set_profiling(r.ctx, True)
     launches0 = G.gbrt_launch_count(r.ctx)
     barrier()
     with ClockSampler(local) as clk:
@@ -300,8 +303,10 @@ def main():
             starts[k].record(stream)
             render_once()
             ends[k].record(stream)
+            phases.append(G.gbrt_phase_times(r.ctx))   # the library's events between its kernels
         barrier()
         wall = time.perf_counter() - t0
+    G.gbrt_set_profiling(r.ctx, False)
     rc = G.gbrt_sync(r.ctx, check=False)
     if rc != G.OK:
         raise SystemExit(f"render reported {G.strerror(rc)}")
@@ -360,14 +365,19 @@ def main():
         cpu = {"value": round(s["rays"] / s["seconds"] / 1e6, 4), "unit": "Mrays/s", "cores": s["cores"],
                "kind": "oracle", "sample": f"{s['rows']} evenly spaced rows ({s['pixels']} px, {s['rays']} rays) "
                                            f"of the same frame, FP64 grid walk, lambda {args.lam}"}
-        fpr, bpr = per_ray_work(s["counters"])
-        kernel_s = dev_s / args.steps
-        achieved = fpr * rays_per_frame / kernel_s / 1e12
-        roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
-                "frac": round(achieved / fp32_peak, 4), "traffic": committed_traffic(args.workload, args.precision),
-                "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz ({peak_src} max clock)",
-                "flops_per_ray": round(fpr, 1), "walk_bytes_per_ray": round(bpr, 1),
-                "walk_GBps": round(bpr * rays_per_frame / kernel_s / 1e9, 1)}
+        # dominant kernel: the AO walk; its algorithmic work per launch is the
+        # AO rays of one frame x the oracle's AO flops per ray (same grid lambda)
+        fpr, bpr = per_ray_work(s["counters"], "ao")
+        ao_rays = rays_per_frame - W * H
+        ao_s = sum(ph["ao_walk"] for ph in phases) / len(phases) / 1e3
+        achieved = fpr * ao_rays / ao_s / 1e12
+        roof = {"bound": "alu", "kernel": "k_ao_walk", "achieved": round(achieved, 3), "peak": round(fp32_peak, 2),
+                "unit": "TFLOP/s", "frac": round(achieved / fp32_peak, 4),
+                "traffic": committed_traffic(args.workload, args.precision),
+                "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz "
+                               f"({peak_src} max clock)",
+                "kernel_ms": round(ao_s * 1e3, 4), "flops_per_ray": round(fpr, 1),
+                "walk_bytes_per_ray": round(bpr, 1), "walk_GBps": round(bpr * ao_rays / ao_s / 1e9, 1)}
 
     line = {"metric": "AO Mrays/s (primary + AO rays) at 1.1 MP, 16 spp", "value": round(value, 3),
             "unit": "Mrays/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -380,6 +390,7 @@ def main():
                        "rays_per_frame": rays_per_frame, "hit_pixels": hits,
                        "l2": "flushed between steps (512 MB write outside the timed events)"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "phases_ms": {k: round(sum(ph[k] for ph in phases) / len(phases), 4) for k in G.PHASES},
             "wall_s_timed_region": round(wall, 4), "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
     r.close()

@@ -294,6 +294,16 @@ GBRT_API int gbrt_render_noalloc(const gbrt_scene* scene, const gbrt_grid* grid,
 GBRT_API int gbrt_set_tuning(gbrt_ctx* ctx, const gbrt_tuning* tuning);
 GBRT_API int gbrt_get_tuning(const gbrt_ctx* ctx, gbrt_tuning* tuning);
 
+/* Per-kernel timing (phase timers): while on, renders record
+ * CUDA events between their kernels on the context's stream (renders replayed
+ * from a CUDA graph are not timed). */
+GBRT_API int gbrt_set_profiling(gbrt_ctx* ctx, int on);
+
+/* Device time in ms of the last timed render's kernels: [0] primary walk and
+ * refinement, [1] AO plan, [2] AO shadow-ray walk, [3] shading. Waits for
+ * that render. GBRT_EINVAL if no render was timed. */
+GBRT_API int gbrt_phase_times(gbrt_ctx* ctx, float ms[4]);
+
 /* Number of kernels this context has launched so far (host counter). */
 GBRT_API int64_t gbrt_launch_count(const gbrt_ctx* ctx);
 

@@ -238,6 +238,8 @@ GBRT_API int gbrt_destroy(gbrt_ctx* ctx) {
     cudaStreamSynchronize(ctx->stream);
     if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
     if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
+    for (int k = 0; k < 5; ++k)
+        if (ctx->ev[k]) cudaEventDestroy(ctx->ev[k]);
     cudaEventDestroy(ctx->staging_done);
     cudaFree(ctx->d_err);
     cudaFreeHost(ctx->h_err);
@@ -447,6 +449,26 @@ GBRT_API int gbrt_set_tuning(gbrt_ctx* ctx, const gbrt_tuning* t) {
 GBRT_API int gbrt_get_tuning(const gbrt_ctx* ctx, gbrt_tuning* t) {
     if (!ctx || !t) return GBRT_EINVAL;
     *t = ctx->tuning;
+    return GBRT_OK;
+}
+
+GBRT_API int gbrt_set_profiling(gbrt_ctx* ctx, int on) {
+    if (!ctx) return GBRT_EINVAL;
+    DeviceGuard g(ctx->device);
+    if (on && !ctx->ev[0]) {
+        for (int k = 0; k < 5; ++k)
+            if (cudaEventCreate(&ctx->ev[k]) != cudaSuccess) return GBRT_EDEVICE;
+    }
+    ctx->profiling = on != 0;
+    return GBRT_OK;
+}
+
+GBRT_API int gbrt_phase_times(gbrt_ctx* ctx, float ms[4]) {
+    if (!ctx || !ms || !ctx->timed) return GBRT_EINVAL;
+    DeviceGuard g(ctx->device);
+    if (cudaEventSynchronize(ctx->ev[4]) != cudaSuccess) return GBRT_EDEVICE;
+    for (int k = 0; k < 4; ++k)
+        if (cudaEventElapsedTime(ms + k, ctx->ev[k], ctx->ev[k + 1]) != cudaSuccess) return GBRT_EDEVICE;
     return GBRT_OK;
 }
 

@@ -42,6 +42,10 @@ struct Ctx {
     bool graph_valid = false;
     long long graph_key = 0;
     BatchDev graph_bd{};
+    // per-kernel timing
+    bool profiling = false;
+    bool timed = false;
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 
 struct Scene {

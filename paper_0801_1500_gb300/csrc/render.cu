@@ -571,17 +571,31 @@ static int enqueue_batch(Ctx* ctx, cudaStream_t stream, int precision, const Bat
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_counters, 0, ctx->counters_bytes_used, stream);
     if (e != cudaSuccess) return err_of(e);
     const int block = ctx->tuning.block;
+    // events between the kernels when timing (never inside a graph capture)
+    const bool tm = ctx->profiling && stream == ctx->stream;
+    auto mark = [&](int k) {
+        if (tm) cudaEventRecord(ctx->ev[k], stream);
+    };
+    mark(0);
     if (precision == GBRT_FP32) {
         k_primary<GBRT_FP32><<<gr.primary, block, 0, stream>>>(bd);
+        mark(1);
         k_ao_plan<<<1, 32, 0, stream>>>(bd);
+        mark(2);
         k_ao_walk<float><<<gr.ao, block, (block / 32) * sizeof(AoWarp<float>), stream>>>(bd);
+        mark(3);
         k_shade<float><<<gr.shade, 256, 0, stream>>>(bd);
     } else {
         k_primary<GBRT_FP64><<<gr.primary, block, 0, stream>>>(bd);
+        mark(1);
         k_ao_plan<<<1, 32, 0, stream>>>(bd);
+        mark(2);
         k_ao_walk<double><<<gr.ao, block, (block / 32) * sizeof(AoWarp<double>), stream>>>(bd);
+        mark(3);
         k_shade<double><<<gr.shade, 256, 0, stream>>>(bd);
     }
+    mark(4);
+    if (tm) ctx->timed = true;
     ctx->launches += 4;
     return err_of(cudaGetLastError());
 }

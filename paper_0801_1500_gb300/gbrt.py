@@ -86,6 +86,8 @@ def _load():
         "gbrt_set_tuning": ([P, C.POINTER(gbrt_tuning)], C.c_int),
         "gbrt_get_tuning": ([P, C.POINTER(gbrt_tuning)], C.c_int),
         "gbrt_launch_count": ([P], C.c_int64),
+        "gbrt_set_profiling": ([P, C.c_int], C.c_int),
+        "gbrt_phase_times": ([P, P], C.c_int),
         "gbrt_render_noalloc": ([P, P, C.POINTER(gbrt_camera), i32, i32, i32, C.POINTER(gbrt_lights),
                                  C.POINTER(gbrt_params), P, P, P, P], C.c_int),
     }
@@ -288,6 +290,20 @@ def gbrt_get_tuning(ctx):
     t = gbrt_tuning()
     _check(lib.gbrt_get_tuning(ctx, C.byref(t)), "gbrt_get_tuning")
     return dict(tile_w=t.tile_w, tile_h=t.tile_h, block=t.block, ctas_per_sm=t.ctas_per_sm, refill=t.refill)
+
+
+def gbrt_set_profiling(ctx, on=True):
+    return _check(lib.gbrt_set_profiling(ctx, 1 if on else 0), "gbrt_set_profiling")
+
+
+PHASES = ("primary", "ao_plan", "ao_walk", "shade")
+
+
+def gbrt_phase_times(ctx):
+    """Per-kernel device times (ms) of the last timed render."""
+    out = (C.c_float * 4)()
+    _check(lib.gbrt_phase_times(ctx, out), "gbrt_phase_times")
+    return dict(zip(PHASES, [float(x) for x in out]))
 
 
 def gbrt_launch_count(ctx) -> int:
