@@ -210,7 +210,7 @@ def run_reference(args, w):
             rays += s["rays"]
     total = sum(times)
     v = rays / total / 1e6
-    line = {"impl": "reference", "metric": "AO Mrays/s (FP64 CPU oracle)", "value": round(v, 4), "unit": "Mrays/s",
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "Mrays/s",
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(1e3 * total / max(1, len(times)), 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -221,25 +221,66 @@ def run_reference(args, w):
     print(json.dumps(line), flush=True)
 
 
+METRIC = "AO Mrays/s & fps at 1.1/17.6 MP, FP32 vs FP64 on GPU; serving p50/p99 latency"
+
+
+def orbit_items(G, torch, dev, scene_h, grid_h, sc, lights, precision, n_frames=64):
+    """The 64-frame orbit: render items plus their rays (primary + AO of hit pixels)."""
+    frames = S.orbit_frames(sc, n_frames)
+    items, outs = [], []
+    for f in frames:
+        p = S.Params(ao_samples=f["spp"], seed=f["seed"], frame=f["frame"], precision=precision)
+        dt = torch.float64 if precision == S.PRECISION_FP64 else torch.float32
+        o = (torch.empty((f["height"], f["width"], 3), dtype=dt, device=dev),
+             torch.empty((f["height"], f["width"]), dtype=torch.int32, device=dev))
+        outs.append(o)
+        items.append(G.make_item(scene_h, grid_h, f["camera"], f["width"], f["height"], f["spp"], lights, p, *o))
+    return frames, items, outs
+
+
+def time_steps(torch, stream, flush, step, steps, warmup, after=None):
+    """Per-step device times (ms): L2 flush outside the events."""
+    for _ in range(warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    extra = []
+    for k in range(steps):
+        flush.zero_()
+        starts[k].record(stream)
+        step()
+        ends[k].record(stream)
+        if after is not None:
+            extra.append(after())
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in zip(starts, ends)], extra
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="paper_1mp")
+    ap.add_argument("--workload", default="paper_1mp", help="paper_1mp | paper_17mp | small | orbit64")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
-    ap.add_argument("--lam", type=float, default=2.0)
-    ap.add_argument("--refill", type=int, default=0, help="AO lane refill threshold (0 = library default)")
+    ap.add_argument("--lam", type=float, default=0.0, help="grid cells per object (0 = autotune)")
+    ap.add_argument("--refill", type=int, default=0, help="AO lane refill threshold (0 = autotune)")
     ap.add_argument("--block", type=int, default=0, help="threads per CTA of the persistent kernels")
     ap.add_argument("--tile", default="", help="primary tile WxH, product 32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the FP64 and 17.6 MP side measurements")
     ap.add_argument("--ref-budget", type=float, default=8.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
-    w = workload(args.workload, args.precision)
+    orbit = args.workload == "orbit64"
+    w = workload("paper_1mp" if orbit else args.workload, args.precision)
 
     if args.impl == "reference":
+        if not args.lam:
+            args.lam = 2.0
         run_reference(args, w)
         return
 
@@ -250,92 +291,104 @@ def main():
         torch.cuda.set_device(local)
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     from paper_0801_1500_gb300 import gbrt as G
+    from paper_0801_1500_gb300 import autotune as AT
 
     dev = torch.device(f"cuda:{local}")
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
     r = G.Renderer(local, stream)
-    tun = G.gbrt_get_tuning(r.ctx)
-    if args.refill:
-        tun["refill"] = args.refill
-    if args.block:
-        tun["block"] = args.block
-    if args.tile:
-        tun["tile_w"], tun["tile_h"] = (int(x) for x in args.tile.split("x"))
-    G.gbrt_set_tuning(r.ctx, **tun)
-    scene, grid = r.upload(w.scene, lam=args.lam)
     W, H, p = w.width, w.height, w.params
     spp = p.ao_samples
-
-    # rays per frame (pixels + AO rays of hit pixels), from one untimed render
-    rgb, ids, _ = r.render(scene, grid, w.camera, W, H, w.lights, p, ids=True)
-    G.gbrt_sync(r.ctx)
-    hits = int((ids.cpu().numpy().view(np.uint32) != G.MISS).sum())
-    rays_per_frame = W * H + hits * spp
+    manual = args.lam or args.refill or args.block or args.tile
+    if manual:
+        tun = G.gbrt_get_tuning(r.ctx)
+        if args.refill:
+            tun["refill"] = args.refill
+        if args.block:
+            tun["block"] = args.block
+        if args.tile:
+            tun["tile_w"], tun["tile_h"] = (int(x) for x in args.tile.split("x"))
+        G.gbrt_set_tuning(r.ctx, **tun)
+        lam = args.lam or 2.0
+        scene, grid = r.upload(w.scene, lam=lam)
+        tuned = {"source": "command line"}
+    else:
+        best, scene, grid = AT.autotune(r, w.scene, w.camera, W, H, w.lights, p)
+        lam = best["lambda"]
+        tuned = {"source": "autotuner", "trials": best.get("trials", 0)}
+    args.lam = lam
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    out = torch.empty((H, W, 3), dtype=torch.float64 if p.precision == S.PRECISION_FP64 else torch.float32,
-                      device=dev)
-    cam, li, pa = G.make_camera(w.camera), G.make_lights(w.lights), G.make_params(p)
-
-    def render_once():
-        G.gbrt_render(r.ctx, scene, grid, cam, W, H, spp, li, pa, out)
-
-    for _ in range(args.warmup):
-        flush.zero_()
-        render_once()
-    G.gbrt_sync(r.ctx)
+    launches0 = G.gbrt_launch_count(r.ctx)
 
     def barrier():
         if ws > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize(dev)
 
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    phases = []
-    G.gbrt_set_profiling(r.ctx, True)
-    launches0 = G.gbrt_launch_count(r.ctx)
-    barrier()
-    with ClockSampler(local) as clk:
-        t0 = time.perf_counter()
-        for k in range(args.steps):
-            flush.zero_()                      # L2 flush between steps, outside the events
-            starts[k].record(stream)
-            render_once()
-            ends[k].record(stream)
-            phases.append(G.gbrt_phase_times(r.ctx))   # the library's events between its kernels
+    if orbit:
+        frames, items, outs = orbit_items(G, torch, dev, scene, grid, w.scene, w.lights, p.precision)
+        G.gbrt_render_batch(r.ctx, items, G.BATCH_GRAPH)
+        G.gbrt_sync(r.ctx)
+        hits = sum(int((o[1].cpu().numpy().view(np.uint32) != G.MISS).sum()) for o in outs)
+        rays_per_step = sum(f["width"] * f["height"] for f in frames) + sum(
+            int((o[1].cpu().numpy().view(np.uint32) != G.MISS).sum()) * f["spp"] for f, o in zip(frames, outs))
+        frames_per_step = len(frames)
         barrier()
-        wall = time.perf_counter() - t0
-    G.gbrt_set_profiling(r.ctx, False)
+        launches0 = G.gbrt_launch_count(r.ctx)
+        with ClockSampler(local) as clk:
+            t0 = time.perf_counter()
+            ms, _ = time_steps(torch, stream, flush, lambda: G.gbrt_render_batch(r.ctx, items, G.BATCH_GRAPH),
+                               args.steps, args.warmup)
+            barrier()
+            wall = time.perf_counter() - t0
+        phases = None
+    else:
+        rgb, ids, _ = r.render(scene, grid, w.camera, W, H, w.lights, p, ids=True)
+        G.gbrt_sync(r.ctx)
+        hits = int((ids.cpu().numpy().view(np.uint32) != G.MISS).sum())
+        rays_per_step = W * H + hits * spp
+        frames_per_step = 1
+        out = torch.empty((H, W, 3), dtype=torch.float64 if p.precision == S.PRECISION_FP64 else torch.float32,
+                          device=dev)
+        cam, li, pa = G.make_camera(w.camera), G.make_lights(w.lights), G.make_params(p)
+        G.gbrt_set_profiling(r.ctx, True)
+        barrier()
+        launches0 = G.gbrt_launch_count(r.ctx)
+        with ClockSampler(local) as clk:
+            t0 = time.perf_counter()
+            ms, phases = time_steps(torch, stream, flush,
+                                    lambda: G.gbrt_render(r.ctx, scene, grid, cam, W, H, spp, li, pa, out),
+                                    args.steps, args.warmup, after=lambda: G.gbrt_phase_times(r.ctx))
+            barrier()
+            wall = time.perf_counter() - t0
+        G.gbrt_set_profiling(r.ctx, False)
     rc = G.gbrt_sync(r.ctx, check=False)
     if rc != G.OK:
         raise SystemExit(f"render reported {G.strerror(rc)}")
-    launches = G.gbrt_launch_count(r.ctx) - launches0
-    ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    # kernels the library launched per timed step (warm-up steps ran in the same window)
+    launches = (G.gbrt_launch_count(r.ctx) - launches0) * args.steps // (args.steps + args.warmup)
     dev_s = sum(ms) / 1e3
     t_rank = torch.tensor([dev_s], dtype=torch.float64, device=dev)
     if ws > 1:
         torch.distributed.all_reduce(t_rank, op=torch.distributed.ReduceOp.MAX)
     t_max = float(t_rank.item())
-    total_rays = rays_per_frame * args.steps * ws
-    value = total_rays / t_max / 1e6
+    value = rays_per_step * args.steps * ws / t_max / 1e6
     ms_step = 1e3 * t_max / args.steps
 
     # e2e: host arrays -> upload -> grid build -> render -> host image, per step
     e2e = None
-    if rank == 0:
+    if rank == 0 and not orbit:
         pinned = {k: torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).pin_memory().numpy().view(a.dtype)
                   for k, a in (("s", w.scene.spheres), ("c", w.scene.cylinders),
                                ("i", w.scene.color_idx), ("p", w.scene.palette))}
         host_out = torch.empty(out.shape, dtype=out.dtype).pin_memory().numpy()
         pa_host = G.make_params(p, out_flags=G.HOST_PTRS)
-        e2e_steps = max(3, min(args.steps, 10))
         tt = []
-        for k in range(e2e_steps + 2):
+        for k in range(max(3, min(args.steps, 10)) + 2):
             torch.cuda.synchronize(dev)
             t1 = time.perf_counter()
             sc2 = G.gbrt_scene_upload(r.ctx, pinned["s"], pinned["c"], pinned["i"], pinned["p"], G.HOST_PTRS)
-            gr2 = G.gbrt_grid_build(r.ctx, sc2, args.lam)
+            gr2 = G.gbrt_grid_build(r.ctx, sc2, lam)
             G.gbrt_render(r.ctx, sc2, gr2, cam, W, H, spp, li, pa_host, host_out)
             t2 = time.perf_counter()
             G.gbrt_grid_free(r.ctx, gr2)
@@ -343,9 +396,10 @@ def main():
             if k >= 2:
                 tt.append(t2 - t1)
         h2d = sum(a.nbytes for a in pinned.values())
-        e2e = {"value": round(rays_per_frame / (sum(tt) / len(tt)) / 1e6, 3), "unit": "Mrays/s",
+        e2e = {"value": round(rays_per_step / (sum(tt) / len(tt)) / 1e6, 3), "unit": "Mrays/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(host_out.nbytes),
-               "ms_per_step": round(1e3 * sum(tt) / len(tt), 3)}
+               "ms_per_step": round(1e3 * sum(tt) / len(tt), 3),
+               "fps": round(1.0 / (sum(tt) / len(tt)), 2)}
 
     if rank != 0:
         r.close()
@@ -358,40 +412,65 @@ def main():
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
 
+    # side measurements on the same GPU: the plain FP64 path and 17.6 MP
+    extras = {}
+    if not args.no_extras and not orbit and args.workload == "paper_1mp":
+        for name, wk in (("fp64_path_1.1MP", S.paper_1mp(precision=S.PRECISION_FP64 if p.precision == S.PRECISION_FP32
+                                                         else S.PRECISION_FP32, scene=w.scene)),
+                         ("fp32_path_17.6MP", S.paper_17mp(precision=S.PRECISION_FP32, scene=w.scene))):
+            o2 = torch.empty((wk.height, wk.width, 3),
+                             dtype=torch.float64 if wk.params.precision == S.PRECISION_FP64 else torch.float32,
+                             device=dev)
+            i2 = torch.empty((wk.height, wk.width), dtype=torch.int32, device=dev)
+            c2, l2, p2 = G.make_camera(wk.camera), G.make_lights(wk.lights), G.make_params(wk.params)
+            G.gbrt_render(r.ctx, scene, grid, c2, wk.width, wk.height, 16, l2, p2, o2, i2)
+            G.gbrt_sync(r.ctx)
+            h2 = int((i2.cpu().numpy().view(np.uint32) != G.MISS).sum())
+            rays2 = wk.width * wk.height + 16 * h2
+            ms2, _ = time_steps(torch, stream, flush,
+                                lambda: G.gbrt_render(r.ctx, scene, grid, c2, wk.width, wk.height, 16, l2, p2, o2),
+                                3, 2)
+            m2 = sum(ms2) / len(ms2)
+            extras[name] = {"Mrays_s": round(rays2 / m2 / 1e3, 2), "ms_per_frame": round(m2, 4),
+                            "fps": round(1e3 / m2, 2), "rays_per_frame": rays2,
+                            "dtype": "f64" if wk.params.precision == S.PRECISION_FP64 else "f32"}
+
     cpu = None
     roof = None
     if not args.no_cpu_baseline:
-        s = oracle_sample(w, args.lam, budget_s=15.0)
+        s = oracle_sample(w, lam, budget_s=15.0)
         cpu = {"value": round(s["rays"] / s["seconds"] / 1e6, 4), "unit": "Mrays/s", "cores": s["cores"],
                "kind": "oracle", "sample": f"{s['rows']} evenly spaced rows ({s['pixels']} px, {s['rays']} rays) "
-                                           f"of the same frame, FP64 grid walk, lambda {args.lam}"}
-        # dominant kernel: the AO walk; its algorithmic work per launch is the
-        # AO rays of one frame x the oracle's AO flops per ray (same grid lambda)
-        fpr, bpr = per_ray_work(s["counters"], "ao")
-        ao_rays = rays_per_frame - W * H
-        ao_s = sum(ph["ao_walk"] for ph in phases) / len(phases) / 1e3
-        achieved = fpr * ao_rays / ao_s / 1e12
-        roof = {"bound": "alu", "kernel": "k_ao_walk", "achieved": round(achieved, 3), "peak": round(fp32_peak, 2),
-                "unit": "TFLOP/s", "frac": round(achieved / fp32_peak, 4),
-                "traffic": committed_traffic(args.workload, args.precision),
-                "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz "
-                               f"({peak_src} max clock)",
-                "kernel_ms": round(ao_s * 1e3, 4), "flops_per_ray": round(fpr, 1),
-                "walk_bytes_per_ray": round(bpr, 1), "walk_GBps": round(bpr * ao_rays / ao_s / 1e9, 1)}
+                                           f"of the 965x1137 frame, FP64 grid walk, lambda {lam}"}
+        if phases:
+            # dominant kernel: the AO walk; its algorithmic work per launch is the
+            # AO rays of one frame x the oracle's AO flops per ray (same grid lambda)
+            fpr, bpr = per_ray_work(s["counters"], "ao")
+            ao_rays = rays_per_step - W * H
+            ao_s = sum(ph["ao_walk"] for ph in phases) / len(phases) / 1e3
+            achieved = fpr * ao_rays / ao_s / 1e12
+            roof = {"bound": "alu", "kernel": "k_ao_walk", "achieved": round(achieved, 3),
+                    "peak": round(fp32_peak, 2), "unit": "TFLOP/s", "frac": round(achieved / fp32_peak, 4),
+                    "traffic": committed_traffic(args.workload, args.precision),
+                    "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 flop x "
+                                   f"{sm_max:.0f} MHz ({peak_src} max clock)",
+                    "kernel_ms": round(ao_s * 1e3, 4), "flops_per_ray": round(fpr, 1),
+                    "walk_bytes_per_ray": round(bpr, 1), "walk_GBps": round(bpr * ao_rays / ao_s / 1e9, 1)}
 
-    line = {"metric": "AO Mrays/s (primary + AO rays) at 1.1 MP, 16 spp", "value": round(value, 3),
-            "unit": "Mrays/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": round(ms_step, 4), "fps": round(1e3 / ms_step, 2), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
-            "data": "synthetic",
-            "config": {"workload": w.name, "width": W, "height": H, "ao_samples": spp,
-                       "objects": w.scene.n_objects, "precision": args.precision, "grid_lambda": args.lam,
-                       "tuning": G.gbrt_get_tuning(r.ctx),
-                       "rays_per_frame": rays_per_frame, "hit_pixels": hits,
-                       "l2": "flushed between steps (512 MB write outside the timed events)"},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-            "phases_ms": {k: round(sum(ph[k] for ph in phases) / len(phases), 4) for k in G.PHASES},
-            "wall_s_timed_region": round(wall, 4), "clocks": clk.summary()}
+    config = {"workload": ("orbit64_" if orbit else "") + w.name, "precision": args.precision,
+              "grid_lambda": lam, "tuning": G.gbrt_get_tuning(r.ctx), "tuned_by": tuned,
+              "rays_per_step": rays_per_step, "frames_per_step": frames_per_step, "hit_pixels": hits,
+              "l2": "flushed between steps (512 MB write outside the timed events)"}
+    if not orbit:
+        config.update(width=W, height=H, ao_samples=spp, objects=w.scene.n_objects)
+    line = {"metric": METRIC, "value": round(value, 3), "unit": "Mrays/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+            "fps": round(frames_per_step * 1e3 / ms_step, 2), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+            "config": config, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "phases_ms": ({k: round(sum(ph[k] for ph in phases) / len(phases), 4) for k in G.PHASES}
+                          if phases else None),
+            "extras": extras or None, "wall_s_timed_region": round(wall, 4), "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
     r.close()
     if ws > 1:
