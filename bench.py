@@ -65,10 +65,14 @@ def dist_env():
     return ws, rank, local
 
 
+KERNEL_SOURCES = ("gbrt_device.cuh", "gbrt_types.h", "render.cu")
+
+
 def sources_hash():
+    """Hash of the sources that define the render kernels."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_0801_1500_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in KERNEL_SOURCES:
         h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 

@@ -129,76 +129,67 @@ __device__ __forceinline__ void cell_range(const float4* aabb, int64_t id, const
 }
 
 // Squared distance from point q to the box [lo, hi].
-__device__ __forceinline__ double box_dist2(const double q[3], const double lo[3], const double hi[3]) {
-    double d2 = 0.0;
-    for (int k = 0; k < 3; ++k) {
-        double e = fmax(fmax(lo[k] - q[k], 0.0), q[k] - hi[k]);
-        d2 += e * e;
-    }
-    return d2;
+__device__ __forceinline__ float box_dist2(float qx, float qy, float qz, const float lo[3], const float hi[3]) {
+    const float ex = fmaxf(fmaxf(lo[0] - qx, 0.0f), qx - hi[0]);
+    const float ey = fmaxf(fmaxf(lo[1] - qy, 0.0f), qy - hi[1]);
+    const float ez = fmaxf(fmaxf(lo[2] - qz, 0.0f), qz - hi[2]);
+    return ex * ex + ey * ey + ez * ez;
 }
 
-// Does object `id` reach into cell (x, y, z)? A superset test in FP64 on the
-// cell box grown by pad: sphere -- distance from the centre to the box <= r;
-// cylinder -- distance from its axis segment to the box <= r (the capsule
-// around the tube; the distance along the segment is convex, minimised by a
-// ternary search and then relaxed by the search's resolution). Any point of an
-// object lies in a cell this test accepts, so a hit is always found there.
-__device__ __forceinline__ bool cell_reached(const double2* obj64, int64_t id, const BuildP& p, const double h[3],
-                                             int x, int y, int z) {
-    const double2* q = obj64 + 4 * id;
-    const double2 q0 = q[0], q1 = q[1], q2 = q[2], q3 = q[3];
-    const double c[3] = {q0.x, q0.y, q1.x};
-    const double r = q1.y, L = q3.y;
-    const double a[3] = {q2.x, q2.y, q3.x};
+// Does object `id` reach into cell (x, y, z)? A superset test on the cell box
+// grown by pad: sphere -- distance from the centre to the box <= r; cylinder --
+// distance from its axis segment to the box <= r (the capsule around the tube).
+// Along the segment that distance is convex and 1-Lipschitz in the axial
+// coordinate, so a ternary search leaves the minimiser inside an interval of
+// width w and the midpoint's distance is at most the minimum + w/2: the test
+// accepts at midpoint distance <= r + w/2 (+ a float rounding margin). Any
+// point of an object lies in a cell this test accepts, so every hit is found.
+__device__ __forceinline__ bool cell_reached(const float4* obj, int64_t id, const BuildP& p, int x, int y, int z) {
+    const float4 A = obj[2 * id], B = obj[2 * id + 1];
     const int ci[3] = {x, y, z};
-    double lo[3], hi[3];
+    float lo[3], hi[3];
     for (int k = 0; k < 3; ++k) {
-        lo[k] = (double)p.lo[k] + ci[k] * h[k] - p.pad;
-        hi[k] = (double)p.lo[k] + (ci[k] + 1) * h[k] + p.pad;
+        lo[k] = p.lo[k] + (float)ci[k] * p.h[k] - p.pad;
+        hi[k] = p.lo[k] + (float)(ci[k] + 1) * p.h[k] + p.pad;
     }
-    const double rr = r + p.pad;
-    if (L == 0.0) return box_dist2(c, lo, hi) <= rr * rr;
-    double s0 = 0.0, s1 = L;
-    for (int it = 0; it < 40; ++it) {
-        double m1 = s0 + (s1 - s0) / 3.0, m2 = s1 - (s1 - s0) / 3.0;
-        double pa[3] = {c[0] + m1 * a[0], c[1] + m1 * a[1], c[2] + m1 * a[2]};
-        double pb[3] = {c[0] + m2 * a[0], c[1] + m2 * a[1], c[2] + m2 * a[2]};
-        if (box_dist2(pa, lo, hi) < box_dist2(pb, lo, hi)) s1 = m2;
+    const float rr = A.w + p.pad;
+    if (B.w == 0.0f) return box_dist2(A.x, A.y, A.z, lo, hi) <= rr * rr;
+    float s0 = 0.0f, s1 = B.w;
+    for (int it = 0; it < 14; ++it) {
+        const float m1 = s0 + (s1 - s0) * (1.0f / 3.0f), m2 = s1 - (s1 - s0) * (1.0f / 3.0f);
+        const float f1 = box_dist2(A.x + m1 * B.x, A.y + m1 * B.y, A.z + m1 * B.z, lo, hi);
+        const float f2 = box_dist2(A.x + m2 * B.x, A.y + m2 * B.y, A.z + m2 * B.z, lo, hi);
+        if (f1 < f2) s1 = m2;
         else s0 = m1;
     }
-    double sm = 0.5 * (s0 + s1);
-    double pm[3] = {c[0] + sm * a[0], c[1] + sm * a[1], c[2] + sm * a[2]};
-    double slack = 1e-6 * (L + 1.0);
-    double lim = rr + slack;
-    return box_dist2(pm, lo, hi) <= lim * lim;
+    const float sm = 0.5f * (s0 + s1);
+    const float lim = rr + 0.5f * (s1 - s0) + 1e-5f * (B.w + 1.0f);
+    return box_dist2(A.x + sm * B.x, A.y + sm * B.y, A.z + sm * B.z, lo, hi) <= lim * lim;
 }
 
-__global__ void __launch_bounds__(256) k_grid_count(const float4* aabb, const double2* obj64, int64_t N, BuildP p,
+__global__ void __launch_bounds__(256) k_grid_count(const float4* aabb, const float4* obj, int64_t N, BuildP p,
                                                      uint32_t* counts) {
     int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= N) return;
     int c0[3], c1[3];
     cell_range(aabb, id, p, c0, c1);
-    const double h[3] = {(double)p.h[0], (double)p.h[1], (double)p.h[2]};
     for (int z = c0[2]; z <= c1[2]; ++z)
         for (int y = c0[1]; y <= c1[1]; ++y)
             for (int x = c0[0]; x <= c1[0]; ++x)
-                if (cell_reached(obj64, id, p, h, x, y, z))
+                if (cell_reached(obj, id, p, x, y, z))
                     atomicAdd(counts + ((int64_t)z * p.n[1] + y) * p.n[0] + x, 1u);
 }
 
-__global__ void __launch_bounds__(256) k_grid_scatter(const float4* aabb, const double2* obj64, int64_t N, BuildP p,
+__global__ void __launch_bounds__(256) k_grid_scatter(const float4* aabb, const float4* obj, int64_t N, BuildP p,
                                                        const uint2* cells, uint32_t* cursor, uint32_t* items) {
     int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= N) return;
     int c0[3], c1[3];
     cell_range(aabb, id, p, c0, c1);
-    const double h[3] = {(double)p.h[0], (double)p.h[1], (double)p.h[2]};
     for (int z = c0[2]; z <= c1[2]; ++z)
         for (int y = c0[1]; y <= c1[1]; ++y)
             for (int x = c0[0]; x <= c1[0]; ++x) {
-                if (!cell_reached(obj64, id, p, h, x, y, z)) continue;
+                if (!cell_reached(obj, id, p, x, y, z)) continue;
                 int64_t c = ((int64_t)z * p.n[1] + y) * p.n[0] + x;
                 uint32_t slot = atomicAdd(cursor + c, 1u);
                 items[cells[c].x + slot] = (uint32_t)id;
@@ -508,7 +499,7 @@ int grid_build(Ctx* ctx, const Scene* s, float lambda, Grid* g) {
         GB_TRY(cudaMalloc(&counts, (size_t)nc * sizeof(uint32_t)));
         GB_TRY(cudaMemsetAsync(counts, 0, (size_t)nc * sizeof(uint32_t), ctx->stream));
         if (N > 0) {
-            k_grid_count<<<(int)((N + 255) / 256), 256, 0, ctx->stream>>>(s->aabb, s->obj64, N, p, counts);
+            k_grid_count<<<(int)((N + 255) / 256), 256, 0, ctx->stream>>>(s->aabb, s->obj, N, p, counts);
             ctx->launches++;
             GB_TRY(cudaGetLastError());
         }
@@ -554,7 +545,7 @@ int grid_build(Ctx* ctx, const Scene* s, float lambda, Grid* g) {
         if (N > 0) {
             cursor = counts;  // reuse as per-cell fill cursor
             GB_TRY(cudaMemsetAsync(cursor, 0, (size_t)nc * sizeof(uint32_t), ctx->stream));
-            k_grid_scatter<<<(int)((N + 255) / 256), 256, 0, ctx->stream>>>(s->aabb, s->obj64, N, p, g->cells,
+            k_grid_scatter<<<(int)((N + 255) / 256), 256, 0, ctx->stream>>>(s->aabb, s->obj, N, p, g->cells,
                                                                             cursor, g->items);
             k_cell_sort<<<(int)((nc + 255) / 256), 256, 0, ctx->stream>>>(g->cells, nc, g->items);
             ctx->launches += 2;
