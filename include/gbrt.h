@@ -41,7 +41,7 @@ extern "C" {
 #define GBRT_API
 #endif
 
-#define GBRT_VERSION 1
+#define GBRT_VERSION 2
 
 /* ---- error codes ---- */
 #define GBRT_OK 0
@@ -130,7 +130,14 @@ typedef struct gbrt_params {
     double background[3];
 } gbrt_params;
 
-/* One frame of a batch (gbrt_render_batch). Fields as for gbrt_render. */
+/* One frame -- or a band of rows of one frame -- in a batch
+ * (gbrt_render_batch). Fields as for gbrt_render, plus:
+ *  row_begin, row_end  render only rows [row_begin, row_end) of the
+ *              width x height image (0, 0 = all rows). Pixels keep their
+ *              whole-image coordinates and sample counters, so the band's
+ *              pixels are exactly those of the whole-frame render; outputs
+ *              are the whole-image buffers and only the band's rows are
+ *              written. */
 typedef struct gbrt_render_item {
     const gbrt_scene* scene;
     const gbrt_grid* grid;
@@ -139,6 +146,8 @@ typedef struct gbrt_render_item {
     int32_t height;
     int32_t ao_samples;
     int32_t reserved;
+    int32_t row_begin;
+    int32_t row_end;
     gbrt_lights lights;
     gbrt_params params;
     void* out_rgb;

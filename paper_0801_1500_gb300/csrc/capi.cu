@@ -74,6 +74,8 @@ FrameDev make_frame(const gbrt_scene* scene, const gbrt_grid* grid, const gbrt_c
     f.cam_kind = cam->kind;
     f.W = W;
     f.H = H;
+    f.row0 = 0;
+    f.rows = H;
     f.spp = spp;
     f.frame = p->frame;
     f.seed_lo = (uint32_t)(p->seed & 0xFFFFFFFFull);
@@ -389,6 +391,9 @@ GBRT_API int gbrt_render_batch(gbrt_ctx* ctx, const gbrt_render_item* items, int
                                   &it.params, it.out_rgb);
         if (rc != GBRT_OK) return rc;
         if (it.params.out_flags != 0) return GBRT_EINVAL;
+        if (!(it.row_begin == 0 && it.row_end == 0) &&
+            !(0 <= it.row_begin && it.row_begin < it.row_end && it.row_end <= it.height))
+            return GBRT_EINVAL;
     }
     DeviceGuard g(ctx->device);
     if (!g.ok) return GBRT_EDEVICE;
@@ -400,6 +405,10 @@ GBRT_API int gbrt_render_batch(gbrt_ctx* ctx, const gbrt_render_item* items, int
             if (it.params.precision != prec) continue;
             frames.push_back(make_frame(it.scene, it.grid, &it.camera, it.width, it.height, it.ao_samples,
                                         &it.lights, &it.params, it.out_rgb, it.out_hit_ids, it.out_ao_visible));
+            if (it.row_end > 0) {
+                frames.back().row0 = it.row_begin;
+                frames.back().rows = it.row_end - it.row_begin;
+            }
         }
         if (frames.empty()) continue;
         int rc = render_frames(ctx, frames.data(), (int)frames.size(), (flags & GBRT_BATCH_GRAPH) != 0);

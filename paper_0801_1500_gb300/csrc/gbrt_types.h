@@ -79,7 +79,9 @@ struct FrameDev {
     void* out_rgb;
     uint32_t* out_ids;
     uint32_t* out_vis;
-    // tiling of this frame into primary-ray work items (tile_w x tile_h = 32)
+    // rows [row0, row0 + rows) of the image are rendered (a band, or all rows);
+    // their tiling into primary-ray work items (tile_w x tile_h = 32)
+    int32_t row0, rows;
     int32_t tiles_x, tiles_y;
     int64_t hit_base;  // first slot of this frame's region of the hit buffers
 };

@@ -161,8 +161,8 @@ __global__ void __launch_bounds__(256) k_primary(const __grid_constant__ BatchDe
         const long long t = item - b.tile_off[f];
         const int tx = (int)(t % F.tiles_x), ty = (int)(t / F.tiles_x);
         const int i = tx * b.tile_w + lane % b.tile_w;
-        const int j = ty * b.tile_h + lane / b.tile_w;
-        const bool inside = i < F.W && j < F.H;
+        const int j = F.row0 + ty * b.tile_h + lane / b.tile_w;
+        const bool inside = i < F.W && j < F.row0 + F.rows;
         V3<double> o64, d64;
         uint32_t id = GBRT_MISS;
         double t64 = 0.0;
@@ -617,9 +617,9 @@ int render_frames(Ctx* ctx, FrameDev* frames, int n, bool use_graph) {
     long long tiles = 0;
     for (int f = 0; f < n; ++f) {
         frames[f].tiles_x = (frames[f].W + tw - 1) / tw;
-        frames[f].tiles_y = (frames[f].H + th - 1) / th;
+        frames[f].tiles_y = (frames[f].rows + th - 1) / th;
         frames[f].hit_base = px;
-        px += (int64_t)frames[f].W * frames[f].H;
+        px += (int64_t)frames[f].W * frames[f].rows;
         tiles += (long long)frames[f].tiles_x * frames[f].tiles_y;
     }
     int rc;

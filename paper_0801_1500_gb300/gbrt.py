@@ -51,6 +51,7 @@ class gbrt_params(C.Structure):
 class gbrt_render_item(C.Structure):
     _fields_ = [("scene", C.c_void_p), ("grid", C.c_void_p), ("camera", gbrt_camera), ("width", C.c_int32),
                 ("height", C.c_int32), ("ao_samples", C.c_int32), ("reserved", C.c_int32),
+                ("row_begin", C.c_int32), ("row_end", C.c_int32),
                 ("lights", gbrt_lights), ("params", gbrt_params), ("out_rgb", C.c_void_p),
                 ("out_hit_ids", C.c_void_p), ("out_ao_visible", C.c_void_p)]
 
@@ -311,9 +312,12 @@ def gbrt_launch_count(ctx) -> int:
 
 
 def make_item(scene, grid, camera, width, height, ao_samples, lights, params, out_rgb, out_hit_ids=None,
-              out_ao_visible=None) -> gbrt_render_item:
+              out_ao_visible=None, rows=None) -> gbrt_render_item:
+    """rows=(begin, end) renders only that band of the image's rows."""
     it = gbrt_render_item()
     it.scene, it.grid = scene, grid
+    if rows is not None:
+        it.row_begin, it.row_end = int(rows[0]), int(rows[1])
     it.camera = camera if isinstance(camera, gbrt_camera) else make_camera(camera)
     it.width, it.height, it.ao_samples = int(width), int(height), int(ao_samples)
     it.lights = lights if isinstance(lights, gbrt_lights) else make_lights(lights)

@@ -1,0 +1,267 @@
+"""Serving loop: resident scenes, HBM-footprint admission, continuous batching.
+
+Render requests (scene, camera, resolution, AO samples, precision) arrive at
+any time. A request is admitted when its device footprint -- its output
+buffers -- fits in the free part of the HBM budget; a request larger than the
+whole budget is rejected. Admitted requests are cut into bands of rows. The
+loop forms waves: each wave takes the next band of every admitted request in
+turn (oldest first) until the wave's ray budget is full, and renders the wave
+as ONE batched launch sequence (``gbrt_render_batch``), so the bands of
+different requests share the GPU. A request that arrives while waves are
+running joins the next wave; it does not wait for earlier requests to finish.
+A band keeps its whole-image pixel coordinates and sample counters, so every
+result is the same whether its request ran alone or in a mix.
+
+The scheduler talks to a backend with four calls (upload, allocate outputs,
+launch a wave, wait for a wave), so its host logic runs under a fake backend
+on a CPU and under ``GpuBackend`` on a GPU.
+"""
+from __future__ import annotations
+
+import collections
+import concurrent.futures as cf
+import dataclasses
+import math
+import threading
+import time
+from typing import List, Optional
+
+import numpy as np
+
+
+class RejectedError(RuntimeError):
+    """The request's device footprint exceeds the whole HBM budget."""
+
+
+@dataclasses.dataclass
+class Request:
+    scene: int
+    camera: object
+    width: int
+    height: int
+    spp: int
+    precision: int = 0          # 0 = FP32 path, 1 = FP64 path
+    seed: int = 0
+    frame: int = 0
+    want_ids: bool = False
+    # filled in by the server
+    rid: int = -1
+    t_submit: float = 0.0
+    t_admit: float = 0.0
+    t_done: float = 0.0
+    rows_issued: int = 0
+    rows_done: int = 0
+    outputs: object = None
+    future: object = None
+
+    def footprint(self) -> int:
+        """Device bytes of the request's outputs (RGB, optional hit ids)."""
+        px = self.width * self.height
+        return px * 3 * (8 if self.precision == 1 else 4) + (px * 4 if self.want_ids else 0)
+
+    def est_rays(self, rows: int, hit_fraction: float = 0.6) -> float:
+        return self.width * rows * (1.0 + hit_fraction * self.spp)
+
+
+@dataclasses.dataclass
+class Band:
+    req: Request
+    row_begin: int
+    row_end: int
+
+
+class Server:
+    """Continuous-batching render server over a backend (see module doc).
+
+    hbm_budget    device bytes available to admitted requests' outputs
+    wave_rays     estimated rays per wave (primary + AO)
+    wave_pixels   pixels per wave (bounds the library's per-wave working memory)
+    band_rows     rows per band
+    max_inflight  waves enqueued ahead of the oldest unfinished one
+    """
+
+    def __init__(self, backend, scenes, hbm_budget: int = 8 << 30, wave_rays: float = 48e6,
+                 wave_pixels: int = 4 << 20, band_rows: int = 64, max_inflight: int = 2):
+        self.b = backend
+        self.handles = [self.b.upload(sc) for sc in scenes]
+        self.hbm_budget = int(hbm_budget)
+        self.wave_rays = float(wave_rays)
+        self.wave_pixels = int(wave_pixels)
+        self.band_rows = int(band_rows)
+        self.max_inflight = int(max_inflight)
+        self.used = 0
+        self.waiting = collections.deque()
+        self.active: List[Request] = []
+        self.inflight = collections.deque()
+        self.completed: List[Request] = []
+        self.rejected = 0
+        self.waves = 0
+        self.cv = threading.Condition()
+        self.stopping = False
+        self._next_id = 0
+        self.thread = threading.Thread(target=self._loop, name="gbrt-serve", daemon=True)
+        self.thread.start()
+
+    # ------------------------------------------------------------ public
+
+    def submit(self, req: Request) -> cf.Future:
+        fut = cf.Future()
+        req.future = fut
+        req.t_submit = time.perf_counter()
+        if not (0 <= req.scene < len(self.handles)):
+            fut.set_exception(ValueError("unknown scene"))
+            return fut
+        if req.footprint() > self.hbm_budget:
+            self.rejected += 1
+            fut.set_exception(RejectedError(f"request needs {req.footprint()} B > budget {self.hbm_budget} B"))
+            return fut
+        with self.cv:
+            req.rid = self._next_id
+            self._next_id += 1
+            self.waiting.append(req)
+            self.cv.notify()
+        return fut
+
+    def close(self, timeout: Optional[float] = None):
+        with self.cv:
+            self.stopping = True
+            self.cv.notify()
+        self.thread.join(timeout)
+
+    def stats(self):
+        lat = np.array([r.t_done - r.t_submit for r in self.completed]) if self.completed else np.zeros(0)
+        q = lambda p: float(np.percentile(lat, p)) if lat.size else float("nan")  # noqa: E731
+        return dict(completed=len(self.completed), rejected=self.rejected, waves=self.waves,
+                    p50_s=q(50), p99_s=q(99), max_s=float(lat.max()) if lat.size else float("nan"))
+
+    # ------------------------------------------------------------ loop
+
+    def _admit(self):
+        """FIFO admission while the oldest waiting request fits."""
+        while self.waiting and self.used + self.waiting[0].footprint() <= self.hbm_budget:
+            req = self.waiting.popleft()
+            req.outputs = self.b.alloc_outputs(req)
+            req.t_admit = time.perf_counter()
+            self.used += req.footprint()
+            self.active.append(req)
+
+    def _build_wave(self) -> List[Band]:
+        """Round-robin bands over admitted requests, oldest first, within the budgets."""
+        bands: List[Band] = []
+        rays = 0.0
+        pixels = 0
+        progress = True
+        while progress:
+            progress = False
+            for req in self.active:
+                if req.rows_issued >= req.height:
+                    continue
+                r0 = req.rows_issued
+                r1 = min(req.height, r0 + self.band_rows)
+                est = req.est_rays(r1 - r0)
+                px = req.width * (r1 - r0)
+                if bands and (rays + est > self.wave_rays or pixels + px > self.wave_pixels):
+                    return bands
+                bands.append(Band(req, r0, r1))
+                req.rows_issued = r1
+                rays += est
+                pixels += px
+                progress = True
+        return bands
+
+    def _retire(self, bands: List[Band]):
+        now = time.perf_counter()
+        for bd in bands:
+            req = bd.req
+            req.rows_done += bd.row_end - bd.row_begin
+            if req.rows_done >= req.height:
+                req.t_done = now
+                self.used -= req.footprint()
+                self.active.remove(req)
+                self.completed.append(req)
+                req.future.set_result(req.outputs)
+
+    def _loop(self):
+        while True:
+            with self.cv:
+                self._admit()
+                bands = self._build_wave()
+                if not bands and not self.inflight:
+                    if self.stopping and not self.waiting and not self.active:
+                        return
+                    self.cv.wait(0.002)
+                    continue
+            if bands:
+                token = self.b.launch([(self.handles[bd.req.scene], bd) for bd in bands])
+                self.inflight.append((token, bands))
+                self.waves += 1
+            # retire finished waves; block on the oldest when too many are queued
+            while self.inflight and (len(self.inflight) > self.max_inflight or not bands or
+                                     self.b.done(self.inflight[0][0])):
+                token, done_bands = self.inflight.popleft()
+                self.b.wait(token)
+                with self.cv:
+                    self._retire(done_bands)
+
+
+class GpuBackend:
+    """Backend over the C ABI: resident scenes/grids, device outputs, one
+    batched launch per wave on the server's own stream."""
+
+    def __init__(self, device: int = 0, lights=None, lam: float = 2.0, tuning: Optional[dict] = None):
+        import torch
+
+        from . import gbrt as G
+        from . import scenes as S
+        self.torch, self.G, self.S = torch, G, S
+        self.device = device
+        self.stream = torch.cuda.Stream(device)
+        self.r = G.Renderer(device, self.stream)
+        if tuning:
+            G.gbrt_set_tuning(self.r.ctx, **tuning)
+        self.lights = lights or S.default_lights()
+        self.lam = lam
+
+    def upload(self, scene):
+        return self.r.upload(scene, lam=self.lam)
+
+    def alloc_outputs(self, req):
+        t = self.torch
+        dev = f"cuda:{self.device}"
+        with t.cuda.stream(self.stream):
+            rgb = t.empty((req.height, req.width, 3), dtype=t.float64 if req.precision == 1 else t.float32,
+                          device=dev)
+            ids = t.empty((req.height, req.width), dtype=t.int32, device=dev) if req.want_ids else None
+        return rgb, ids
+
+    def params(self, req):
+        return self.S.Params(ao_samples=req.spp, seed=req.seed, frame=req.frame, precision=req.precision)
+
+    def launch(self, work):
+        G = self.G
+        items = []
+        for (scene_h, grid_h), bd in work:
+            req = bd.req
+            rgb, ids = req.outputs
+            items.append(G.make_item(scene_h, grid_h, req.camera, req.width, req.height, req.spp, self.lights,
+                                     self.params(req), rgb, ids, rows=(bd.row_begin, bd.row_end)))
+        G.gbrt_render_batch(self.r.ctx, items)
+        ev = self.torch.cuda.Event()
+        ev.record(self.stream)
+        return ev
+
+    def done(self, ev) -> bool:
+        return ev.query()
+
+    def wait(self, ev):
+        ev.synchronize()
+
+    def close(self):
+        self.G.gbrt_sync(self.r.ctx)
+        self.r.close()
+
+
+def latency_summary(reqs: List[Request]):
+    lat = np.array([r.t_done - r.t_submit for r in reqs])
+    return dict(n=len(reqs), p50_ms=float(np.percentile(lat, 50) * 1e3), p99_ms=float(np.percentile(lat, 99) * 1e3),
+                max_ms=float(lat.max() * 1e3), mean_ms=float(lat.mean() * 1e3))

@@ -84,3 +84,26 @@ def test_batch_with_two_scenes(G):
         G.gbrt_sync(r.ctx)
         for (x0, x1), (y0, y1) in zip(solo, outs):
             assert torch.equal(x0, y0) and torch.equal(x1, y1)
+
+
+def test_bands_equal_whole_frame(G):
+    import torch
+    sc = S.globule(500, 475, 14.0, seed=3)
+    lights = S.default_lights()
+    W, H = 90, 77
+    with G.Renderer(0) as r:
+        scene, grid = r.upload(sc, lam=2.0)
+        for prec in (S.PRECISION_FP32, S.PRECISION_FP64):
+            p = S.Params(ao_samples=7, seed=5, precision=prec)
+            cam = S.ortho_camera(sc, W, H, angle_deg=20.0)
+            ref = r.render(scene, grid, cam, W, H, lights, p, ids=True, vis=True)
+            dt = torch.float64 if prec == S.PRECISION_FP64 else torch.float32
+            o = (torch.full((H, W, 3), -1, dtype=dt, device="cuda"),
+                 torch.full((H, W), -7, dtype=torch.int32, device="cuda"),
+                 torch.full((H, W), -7, dtype=torch.int32, device="cuda"))
+            bands = [(0, 5), (5, 6), (6, 40), (40, 77)]
+            items = [G.make_item(scene, grid, cam, W, H, 7, lights, p, *o, rows=b) for b in bands[::-1]]
+            G.gbrt_render_batch(r.ctx, items)
+            G.gbrt_sync(r.ctx)
+            for x, y in zip(ref, o):
+                assert torch.equal(x, y)
