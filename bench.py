@@ -262,6 +262,85 @@ def time_steps(torch, stream, flush, step, steps, warmup, after=None):
     return [a.elapsed_time(b) for a, b in zip(starts, ends)], extra
 
 
+def replay(srv, SV, reqs_spec, scenes, precision):
+    """Submit a trace in real time (arrival offsets in seconds); wait for all."""
+    import torch
+    reqs, futs = [], []
+    t0 = time.perf_counter()
+    for spec in reqs_spec:
+        delay = spec["arrival_s"] - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        sc = scenes[spec["scene"]]
+        cam = S.ortho_camera(sc, spec["width"], spec["height"], angle_deg=spec.get("angle_deg", 0.0))
+        rq = SV.Request(scene=spec["scene"], camera=cam, width=spec["width"], height=spec["height"],
+                        spp=spec["spp"], precision=precision, seed=spec["id"], want_ids=True)
+        reqs.append(rq)
+        futs.append(srv.submit(rq))
+    done = []
+    rays = 0
+    for rq, f in zip(reqs, futs):
+        try:
+            rgb, ids = f.result(timeout=3600)
+        except SV.RejectedError:
+            continue
+        hits = int((ids != -1).sum().item())
+        rays += rq.width * rq.height + hits * rq.spp
+        done.append(rq)
+    t1 = time.perf_counter()
+    lat = np.array([r.t_done - r.t_submit for r in done]) if done else np.zeros(1)
+    return {"requests": len(reqs_spec), "completed": len(done), "rejected": len(reqs_spec) - len(done),
+            "p50_ms": round(float(np.percentile(lat, 50)) * 1e3, 2),
+            "p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 2),
+            "max_ms": round(float(lat.max()) * 1e3, 2), "wall_s": round(t1 - t0, 3),
+            "Mrays_s": round(rays / (t1 - t0) / 1e6, 1), "waves": srv.stats()["waves"]}
+
+
+def run_serve(args):
+    """Serving stream over 8 resident scenes (1k-250k objects): Poisson
+    arrivals, mixed resolutions and sample counts, admitted by HBM footprint."""
+    import torch
+    from paper_0801_1500_gb300 import serve as SV
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    prec = S.PRECISION_FP64 if args.precision == "fp64" else S.PRECISION_FP32
+    scenes = S.serving_scenes(8, 1000, 250000, seed=0)
+    out = {"metric": METRIC, "unit": "ms", "higher_is_better": False, "n_gpus": ws, "data": "synthetic",
+           "dtype": "f32" if prec == S.PRECISION_FP32 else "f64",
+           "config": {"workload": "serve_8scenes_1k-250k_poisson", "objects": [s.n_objects for s in scenes],
+                      "resolutions": S.SERVE_RESOLUTIONS, "spp": S.SERVE_SPP, "hbm_budget_GB": args.hbm_gb,
+                      "grid_lambda": args.lam or 2.0}}
+    with ClockSampler(local) as clk:
+        # the offered stream at several rates (the highest is the configured rate)
+        sweep = []
+        for rate in args.rates:
+            be = SV.GpuBackend(local, lam=args.lam or 2.0)
+            srv = SV.Server(be, scenes, hbm_budget=int(args.hbm_gb * (1 << 30)))
+            trace = S.poisson_trace(args.requests, rate, len(scenes), seed=0)
+            res = replay(srv, SV, trace, scenes, prec)
+            srv.close()
+            be.close()
+            res["rate_req_s"] = rate
+            sweep.append(res)
+        # a steady 1.1 MP, 16-sample stream on the paper-sized scene at 30 frames/s, then unthrottled
+        paper = [S.paper_scene(0)]
+        steady = {}
+        for label, rate, n in (("30fps", 30.0, 90), ("unthrottled", 1e6, 240)):
+            be = SV.GpuBackend(local, lam=4.0)
+            srv = SV.Server(be, paper, hbm_budget=int(args.hbm_gb * (1 << 30)), wave_rays=24e6, band_rows=1137)
+            trace = [dict(id=k, arrival_s=k / rate, scene=0, width=965, height=1137, spp=16, angle_deg=0.0)
+                     for k in range(n)]
+            res = replay(srv, SV, trace, paper, prec)
+            srv.close()
+            be.close()
+            res["fps"] = round(res["completed"] / res["wall_s"], 1)
+            steady[label] = res
+    main_res = sweep[-1]
+    out.update(value=main_res["p99_ms"], steps=len(sweep), warmup=0,
+               serving={"rate_sweep": sweep, "paper_scene_1.1MP_16spp": steady}, clocks=clk.summary())
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -277,8 +356,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 and 17.6 MP side measurements")
     ap.add_argument("--ref-budget", type=float, default=8.0)
+    ap.add_argument("--requests", type=int, default=200, help="serve: requests per offered rate")
+    ap.add_argument("--rates", type=float, nargs="+", default=[25.0, 50.0, 100.0, 200.0],
+                    help="serve: offered request rates (req/s)")
+    ap.add_argument("--hbm-gb", type=float, default=16.0, help="serve: HBM budget for outputs")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.workload == "serve" and args.impl == "ours":
+        run_serve(args)
+        return
     orbit = args.workload == "orbit64"
     w = workload("paper_1mp" if orbit else args.workload, args.precision)
 
@@ -372,10 +458,8 @@ def main():
     # kernels the library launched per timed step (warm-up steps ran in the same window)
     launches = (G.gbrt_launch_count(r.ctx) - launches0) * args.steps // (args.steps + args.warmup)
     dev_s = sum(ms) / 1e3
-    t_rank = torch.tensor([dev_s], dtype=torch.float64, device=dev)
-    if ws > 1:
-        torch.distributed.all_reduce(t_rank, op=torch.distributed.ReduceOp.MAX)
-    t_max = float(t_rank.item())
+    from paper_0801_1500_gb300 import partition
+    t_max = partition.max_over_ranks(dev_s)
     value = rays_per_step * args.steps * ws / t_max / 1e6
     ms_step = 1e3 * t_max / args.steps
 
