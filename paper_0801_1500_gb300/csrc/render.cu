@@ -62,26 +62,58 @@ __device__ __forceinline__ V3<float> view_dir_f(const FrameDev& f, uint32_t q) {
     return rsqrtf(dot(d, d)) * d;
 }
 
+// FP64 root of object `id`'s quadratic along o + t d by Newton's method from
+// an FP32 root t: F(t) = |w_p(t)|^2 - r^2 with w(t) = o + t d - p0 and w_p its
+// part perpendicular to the axis a (all of w for a sphere, a = 0);
+// F'(t) = 2 d_p . w_p. F and F' are evaluated in FP64; the small correction
+// F/F' is divided in FP32 (its relative error stays far below FP64 rounding of
+// t). Two steps carry an FP32-accurate root to FP64 accuracy on non-grazing
+// rays. False when the steps do not settle (a grazing ray): the caller keeps
+// the FP32 root.
+__device__ __forceinline__ bool newton_root64(const double2* obj64, uint32_t id, V3<double> o, V3<double> d,
+                                              double& t) {
+    V3<double> p0, a;
+    double L, r;
+    Obj<double>::load(obj64, id, p0, a, L, r);
+    const V3<double> f0 = o - p0;
+    const double da = dot(d, a);
+    const V3<double> dp = madd(d, -da, a);
+    double tt = t, corr = 0.0;
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const V3<double> w = madd(f0, tt, d);
+        const V3<double> wp = madd(w, -dot(w, a), a);
+        const double F = dot(wp, wp) - r * r;
+        const double Fp = 2.0 * dot(dp, wp);
+        corr = (double)__fdividef((float)F, (float)Fp);
+        tt -= corr;
+    }
+    const bool ok = fabs(corr) <= 1e-6 * (fabs(tt) + 1.0) && isfinite(tt);
+    if (ok) t = tt;
+    return ok;
+}
+
 // FP32 path: nearest hit in FP32 from the FP32 ray re-based at the grid entry
 // (one FP64 point rounded once, so coordinates stay small relative to the
 // scene), then the winner -- and a runner-up within a relative 1e-4 band --
-// re-solved as an FP64 quadratic from the FP64 ray.
+// carried to its FP64 root (newton_root64) along the FP64 ray.
 __device__ __forceinline__ bool nearest_fp32_refined(const FrameDev& f, V3<double> o64, V3<double> d64,
-                                                     uint32_t& id, double& t64, bool& overflow) {
+                                                     V3<float> df, uint32_t& id, double& t64, bool& overflow) {
     const float inf = Num<float>::inf();
-    V3<float> of = to_f(o64), df = to_f(d64);
+    V3<float> of = to_f(o64);
     float te0, te1;
     if (!clip_grid<float>(f.grid, of, df, 0.0f, inf, te0, te1)) return false;
     V3<float> oe = to_f(madd(o64, (double)te0, d64));
     Nearest<float> h;
     if (!trace_nearest<float>(f.grid, f.scene, oe, df, 0.0f, inf, h, overflow)) return false;
-    double ta = 0.0, tb = 0.0;
-    bool ok1 = hit_object<double>(f.scene, h.id1, o64, d64, 0.0, Num<double>::inf(), ta);
+    double ta = (double)te0 + (double)h.t1;
+    newton_root64(f.scene.obj64, h.id1, o64, d64, ta);
     id = h.id1;
-    t64 = ok1 ? ta : (double)te0 + (double)h.t1;  // FP64 disagrees only on grazing rays
+    t64 = ta;
     if (h.id2 != GBRT_MISS && (h.t2 - h.t1) <= 1e-4f * (h.t1 + te0)) {
-        bool ok2 = hit_object<double>(f.scene, h.id2, o64, d64, 0.0, Num<double>::inf(), tb);
-        if (ok2 && (!ok1 || tb < ta || (tb == ta && h.id2 < h.id1))) {
+        double tb = (double)te0 + (double)h.t2;
+        newton_root64(f.scene.obj64, h.id2, o64, d64, tb);
+        if (tb < ta || (tb == ta && h.id2 < h.id1)) {
             id = h.id2;
             t64 = tb;
         }
@@ -170,7 +202,8 @@ __global__ void __launch_bounds__(256) k_primary(const __grid_constant__ BatchDe
         if (inside) {
             primary_ray64(F, i, j, o64, d64);
             if (MODE == GBRT_FP32) {
-                hit = nearest_fp32_refined(F, o64, d64, id, t64, overflow);
+                hit = nearest_fp32_refined(F, o64, d64, view_dir_f(F, (uint32_t)j * (uint32_t)F.W + (uint32_t)i),
+                                           id, t64, overflow);
             } else {
                 Nearest<double> h;
                 hit = trace_nearest<double>(F.grid, F.scene, o64, d64, 0.0, Num<double>::inf(), h, overflow);
@@ -193,24 +226,24 @@ __global__ void __launch_bounds__(256) k_primary(const __grid_constant__ BatchDe
             V3<double> ao_o, n;
             bool inside_hit = false;
             if (MODE == GBRT_FP32) {
-                // FP64 hit point and its foot q on the generator (centre or axis);
-                // the outward unit normal in FP32; the surface point q + r n_out
-                // and the AO origin one eps along the normal facing the ray
+                // FP64 hit point and its foot q on the generator (centre or
+                // axis); the outward unit normal in FP32; the AO origin one eps
+                // along the normal facing the ray from the re-projected
+                // surface point q + r n_out
                 V3<double> p0, a;
                 double L, r;
                 Obj<double>::load(F.scene.obj64, id, p0, a, L, r);
-                V3<double> p = madd(o64, t64, d64);
-                V3<double> qq = madd(p0, dot(p - p0, a), a);
-                V3<float> nf = to_f(p - qq);
+                const V3<double> w = madd(o64 - p0, t64, d64);
+                const V3<double> qq = madd(p0, dot(w, a), a);
+                V3<float> nf = to_f(madd(w, -dot(w, a), a));
                 nf = rsqrtf(dot(nf, nf)) * nf;
-                const V3<double> n_out = to_d(nf);
-                const V3<double> ps = madd(qq, r, n_out);
-                if (dot(to_f(d64), nf) > 0.0f) {
-                    nf = v3(-nf.x, -nf.y, -nf.z);
-                    inside_hit = true;
-                }
-                n = to_d(nf);
-                ao_o = madd(ps, F.eps, n);
+                const V3<float> dfv = view_dir_f(F, q);
+                const bool flip = dot(dfv, nf) > 0.0f;
+                inside_hit = flip;
+                // surface point + eps n_face = q + (r n_out) + eps n_face
+                const double off = flip ? r - F.eps : r + F.eps;
+                n = to_d(flip ? v3(-nf.x, -nf.y, -nf.z) : nf);
+                ao_o = madd(qq, off, to_d(nf));
             } else {
                 V3<double> p;
                 inside_hit = reproject64(F.scene, id, o64, d64, t64, p, n);
