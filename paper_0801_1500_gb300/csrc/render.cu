@@ -132,9 +132,13 @@ template <>
 struct HitIO<float> {
     static __device__ __forceinline__ void store(void* hits, int64_t slot, V3<double> o, V3<double> n, uint32_t q,
                                                  uint32_t id) {
+        store_f(hits, slot, o, to_f(n), q, id);
+    }
+    static __device__ __forceinline__ void store_f(void* hits, int64_t slot, V3<double> o, V3<float> n, uint32_t q,
+                                                   uint32_t id) {
         float4* H = (float4*)hits + 2 * slot;
         H[0] = make_float4((float)o.x, (float)o.y, (float)o.z, __uint_as_float(q));
-        H[1] = make_float4((float)n.x, (float)n.y, (float)n.z, __uint_as_float(id));
+        H[1] = make_float4(n.x, n.y, n.z, __uint_as_float(id));
     }
     static __device__ __forceinline__ void load(const void* hits, int64_t slot, V3<float>& o, V3<float>& n,
                                                 uint32_t& q, uint32_t& id) {
@@ -223,8 +227,6 @@ __global__ void __launch_bounds__(256) k_primary(const __grid_constant__ BatchDe
         const uint32_t q = (uint32_t)j * (uint32_t)F.W + (uint32_t)i;
         if (hit) {
             const int64_t slot = F.hit_base + base + __popc(hm & ((1u << lane) - 1u));
-            V3<double> ao_o, n;
-            bool inside_hit = false;
             if (MODE == GBRT_FP32) {
                 // FP64 hit point and its foot q on the generator (centre or
                 // axis); the outward unit normal in FP32; the AO origin one eps
@@ -234,22 +236,20 @@ __global__ void __launch_bounds__(256) k_primary(const __grid_constant__ BatchDe
                 double L, r;
                 Obj<double>::load(F.scene.obj64, id, p0, a, L, r);
                 const V3<double> w = madd(o64 - p0, t64, d64);
-                const V3<double> qq = madd(p0, dot(w, a), a);
-                V3<float> nf = to_f(madd(w, -dot(w, a), a));
+                const double wa = dot(w, a);
+                const V3<double> qq = madd(p0, wa, a);
+                V3<float> nf = to_f(madd(w, -wa, a));
                 nf = rsqrtf(dot(nf, nf)) * nf;
-                const V3<float> dfv = view_dir_f(F, q);
-                const bool flip = dot(dfv, nf) > 0.0f;
-                inside_hit = flip;
-                // surface point + eps n_face = q + (r n_out) + eps n_face
-                const double off = flip ? r - F.eps : r + F.eps;
-                n = to_d(flip ? v3(-nf.x, -nf.y, -nf.z) : nf);
-                ao_o = madd(qq, off, to_d(nf));
+                const bool flip = dot(view_dir_f(F, q), nf) > 0.0f;
+                // surface point + eps n_face = q + r n_out + eps n_face
+                const V3<double> ao_o = madd(qq, flip ? r - F.eps : r + F.eps, to_d(nf));
+                if (flip) nf = v3(-nf.x, -nf.y, -nf.z);
+                HitIO<float>::store_f(b.hits, slot, ao_o, nf, q | (flip ? HIT_INSIDE : 0u), id);
             } else {
-                V3<double> p;
-                inside_hit = reproject64(F.scene, id, o64, d64, t64, p, n);
-                ao_o = madd(p, F.eps, n);
+                V3<double> p, n;
+                const bool inside_hit = reproject64(F.scene, id, o64, d64, t64, p, n);
+                HitIO<R>::store(b.hits, slot, madd(p, F.eps, n), n, q | (inside_hit ? HIT_INSIDE : 0u), id);
             }
-            HitIO<R>::store(b.hits, slot, ao_o, n, q | (inside_hit ? HIT_INSIDE : 0u), id);
             b.vis[slot] = 0u;
             if (F.out_ids) F.out_ids[q] = id;
         } else {
