@@ -306,7 +306,7 @@ struct __align__(16) AoRay {
 //                words so distinct rays and slots fall in distinct banks); a
 //                re-test of a missed object cannot hit, so skipping it is exact
 //   qr/qid       surviving (ray, object) pairs waiting for a full test batch
-constexpr int AO_MBOX = 16;
+constexpr int AO_MBOX = 8;
 
 template <class R>
 struct AoWarp {
