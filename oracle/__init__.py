@@ -194,7 +194,7 @@ def camera_vector(cam):
 
 
 def shade_vector(lights, params):
-    sp = np.zeros(11)
+    sp = np.zeros(12)
     sp[0] = lights.scale
     sp[1] = lights.skylight
     sp[2] = params.k_ao
@@ -204,6 +204,7 @@ def shade_vector(lights, params):
     sp[6] = params.eps
     sp[7] = params.ao_maxdist
     sp[8:11] = params.background
+    sp[11] = 1.0 if getattr(params, "shadows", False) else 0.0
     return sp
 
 

@@ -586,18 +586,19 @@ static void primary_ray(const double* cam, int W, int H, int64_t i, int64_t j, d
 /* Shading: Phong with directional lights scaled by light_scale plus an AO   */
 /* skylight term (paper Sec. 2: -rescale_lights, -add_skylight, AO).          */
 /*  sp: [0] light_scale [1] skylight [2] k_ao [3] k_d [4] k_s [5] phong_exp  */
-/*      [6] eps [7] ao_maxdist [8..10] background rgb                        */
+/*      [6] eps [7] ao_maxdist [8..10] background rgb [11] shadows (0/1)     */
+/* lit[l] = 0 drops light l (its shadow ray was blocked).                     */
 /* ------------------------------------------------------------------------ */
 
 static void shade(const double albedo[3], const double n[3], const double d[3], double V,
-                  const double* ldir, const double* lI, int nl, const double* sp, double rgb[3])
+                  const double* ldir, const double* lI, int nl, const double* sp, const int* lit, double rgb[3])
 {
     double diff = 0.0, spec = 0.0;
     double v[3] = {-d[0], -d[1], -d[2]};
     for (int l = 0; l < nl; ++l) {
         const double* L = ldir + 3 * l;
         double ndl = dot3(n, L);
-        if (ndl <= 0.0) continue;
+        if (ndl <= 0.0 || !lit[l]) continue;
         diff += sp[0] * lI[l] * sp[3] * ndl;
         double r[3] = {2.0 * ndl * n[0] - L[0], 2.0 * ndl * n[1] - L[1], 2.0 * ndl * n[2] - L[2]};
         double rv = dot3(r, v);
@@ -814,9 +815,19 @@ int oracle_render(int64_t S, const double* sph, int64_t C, const double* cyl,
                 loc[1] += spp;
                 loc[6] += ac.cells; loc[7] += ac.sph; loc[8] += ac.cyl; loc[9] += vis;
                 double V = spp > 0 ? (double)vis / spp : 1.0;
+                /* direct-light shadow rays: from the AO origin toward each light
+                 * the surface faces; any hit (0 < t) blocks that light */
+                int lit[64];
+                for (int l = 0; l < nl && l < 64; ++l) {
+                    lit[l] = 1;
+                    if (sp[11] != 0.0 && dot3(n, ldir + 3 * l) > 0.0) {
+                        ocount sc_ = {0, 0, 0};
+                        lit[l] = !world_anyhit(&w, ao_o, ldir + 3 * l, INFINITY, &sc_);
+                    }
+                }
                 uint32_t ci = w.sc.color[nr.id1];
                 double albedo[3] = {palette[3 * ci], palette[3 * ci + 1], palette[3 * ci + 2]};
-                shade(albedo, n, d, V, ldir, lI, nl, sp, rgb);
+                shade(albedo, n, d, V, ldir, lI, nl, sp, lit, rgb);
             }
             if (out_rgb) { out_rgb[3 * k] = rgb[0]; out_rgb[3 * k + 1] = rgb[1]; out_rgb[3 * k + 2] = rgb[2]; }
             if (out_id) out_id[k] = nr.id1;

@@ -261,6 +261,7 @@ class Params:
     k_s: float = 0.4
     phong_exp: float = 40.0
     background: tuple = (0.0, 0.0, 0.0)
+    shadows: bool = False    # direct-light shadow rays (one per light the surface faces)
 
 
 # --------------------------------------------------------------------------

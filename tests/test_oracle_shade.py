@@ -107,3 +107,56 @@ def test_zero_samples_means_open_sky(oracle):
     ref = oracle.render(sc, cam(), W, H, S.default_lights(), p1, pixels=[25 * W + 20], mode="brute")
     assert out["vis"][0] == 0
     assert np.all(out["rgb"][0] >= ref["rgb"][0] - 1e-12)
+
+
+def test_direct_light_shadow_of_a_sphere(oracle):
+    # sphere B sits between sphere A and light 1 (straight toward the camera
+    # side): points of A whose ray toward light 1 meets B lose light 1; the
+    # blocked set is found here by the closed-form line-sphere distance
+    rA, rB = 2.0, 0.9
+    L1 = np.array([0.0, 0.0, 1.0])
+    L2 = np.array([0.6, 0.0, 0.8])
+    lights = S.Lights(dirs=[tuple(L1), tuple(L2)], intensity=[1.0, 1.0])
+    B = np.array([0.3, 0.2, 4.0])
+    sc = S.make_scene([[0, 0, 0, rA], [B[0], B[1], B[2], rB]], palette=[[0.7, 0.6, 0.5]])
+    c = rotated_cam(30.0)   # looks at A from the side so B does not hide A's centre
+    right, up, view = np.array(c.right), np.array(c.up), -np.array(c.dir)
+    pix, expect = [], []
+    for i in range(5, 46, 4):
+        for j in range(5, 46, 4):
+            u, v = 0.1 * (i + 0.5) - HALF, HALF - 0.1 * (j + 0.5)
+            if u * u + v * v >= (0.97 * rA) ** 2:
+                continue
+            z = math.sqrt(rA * rA - u * u - v * v)
+            n = (u * right + v * up + z * view) / rA
+            pnt = rA * n
+            # the camera ray must meet A first (B is elsewhere along it)
+            o = pnt + 10.0 * view
+            f = o - B
+            b = f @ (-view)
+            if (f @ f - b * b) < rB * rB and b < 0:
+                continue
+            diff = spec = 0.0
+            for Ld in (L1, L2):
+                ndl = n @ Ld
+                if ndl <= 0:
+                    continue
+                fb = pnt + 1e-3 * n - B
+                bb = fb @ Ld
+                blocked = (fb @ fb - bb * bb) < rB * rB and bb < 0
+                if blocked:
+                    continue
+                diff += 0.3 * 0.65 * ndl
+                refl = 2 * ndl * n - Ld
+                spec += 0.3 * 0.4 * max(0.0, refl @ view) ** 40
+            pix.append(j * W + i)
+            expect.append(np.clip(np.array([0.7, 0.6, 0.5]) * (0.6 + diff) + spec, 0, 1))
+    p = S.Params(ao_samples=0, shadows=True, precision=S.PRECISION_FP64)
+    out = oracle.render(sc, c, W, H, lights, p, pixels=pix, mode="brute")
+    assert np.all(out["id"] == 0)
+    assert np.allclose(out["rgb"], np.array(expect), atol=1e-9)
+    # some of the sampled points are in B's shadow, some are not
+    p0 = S.Params(ao_samples=0, shadows=False, precision=S.PRECISION_FP64)
+    unshadowed = oracle.render(sc, c, W, H, lights, p0, pixels=pix, mode="brute")
+    changed = np.any(np.abs(unshadowed["rgb"] - out["rgb"]) > 1e-6, axis=1)
+    assert 0 < changed.sum() < len(pix)
