@@ -113,6 +113,9 @@ typedef struct gbrt_lights {
  *      with V the fraction of AO samples that escape (V = 1 when
  *      ao_samples = 0), r_l the mirror of l about n, v = -ray direction
  *  background  colour of pixels whose primary ray hits nothing
+ *  shadows     1: direct-light shadow rays -- from the AO origin, one ray per
+ *              light the surface faces; any hit (0 < t) drops that light's
+ *              diffuse and specular terms. 0: lights are never blocked
  *  out_flags   GBRT_HOST_PTRS: the render's output pointers are host memory
  *              (the call then synchronises). */
 typedef struct gbrt_params {
@@ -120,7 +123,7 @@ typedef struct gbrt_params {
     int32_t out_flags;
     uint64_t seed;
     uint32_t frame;
-    uint32_t reserved;
+    int32_t shadows;
     double eps;
     double ao_maxdist;
     double k_ao;

@@ -77,6 +77,8 @@ FrameDev make_frame(const gbrt_scene* scene, const gbrt_grid* grid, const gbrt_c
     f.row0 = 0;
     f.rows = H;
     f.spp = spp;
+    f.shadows = p->shadows ? 1 : 0;
+    f.jobs_per_hit = spp + (f.shadows ? lights->n : 0);
     f.frame = p->frame;
     f.seed_lo = (uint32_t)(p->seed & 0xFFFFFFFFull);
     f.seed_hi = (uint32_t)(p->seed >> 32);
@@ -248,6 +250,7 @@ GBRT_API int gbrt_destroy(gbrt_ctx* ctx) {
     cudaFree(ctx->d_out);
     cudaFree(ctx->d_hits);
     cudaFree(ctx->d_vis);
+    cudaFree(ctx->d_lmask);
     cudaFree(ctx->d_desc);
     cudaFreeHost(ctx->h_desc);
     cudaFree(ctx->d_counters);

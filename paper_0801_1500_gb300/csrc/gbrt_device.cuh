@@ -498,14 +498,15 @@ struct ShadeP<double> {
 
 // colour = clamp01(albedo (skylight k_ao V + sum_l s I_l k_d max(0, n.l))
 //                  + sum_{n.l > 0} s I_l k_s max(0, r_l.v)^p), r_l = 2 (n.l) n - l
+// lit: bit l clear drops light l (its shadow ray was blocked).
 template <class R>
-__device__ __forceinline__ void shade(const FrameDev& f, uint32_t id, V3<R> n, V3<R> d, R V, R rgb[3]) {
+__device__ __forceinline__ void shade(const FrameDev& f, uint32_t id, V3<R> n, V3<R> d, R V, uint32_t lit, R rgb[3]) {
     R diff = R(0), spec = R(0);
     V3<R> v = v3(-d.x, -d.y, -d.z);
     for (int l = 0; l < f.nl; ++l) {
         V3<R> L = ShadeP<R>::ldir(f, l);
         R ndl = dot(n, L);
-        if (ndl <= R(0)) continue;
+        if (ndl <= R(0) || !((lit >> l) & 1u)) continue;
         R I = ShadeP<R>::lI(f, l);
         diff += I * ShadeP<R>::k_d(f) * ndl;
         V3<R> r = madd(v3(-L.x, -L.y, -L.z), R(2) * ndl, n);

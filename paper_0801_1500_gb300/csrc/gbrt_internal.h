@@ -27,6 +27,8 @@ struct Ctx {
     size_t hits_cap = 0;
     unsigned int* d_vis = nullptr;
     size_t vis_cap = 0;
+    unsigned int* d_lmask = nullptr;
+    size_t lmask_cap = 0;
     void* d_desc = nullptr;
     size_t desc_cap = 0;
     void* h_desc = nullptr;  // pinned staging of the descriptors

@@ -60,6 +60,8 @@ struct FrameDev {
     float half_w_f, half_h_f, inv_w_f, inv_h_f;
     int32_t cam_kind;
     int32_t W, H, spp;
+    int32_t shadows;       // 1: one shadow ray per light the surface faces
+    int32_t jobs_per_hit;  // AO samples + shadow rays of one hit
     uint32_t frame;
     uint32_t seed_lo, seed_hi;
     int32_t precision;
@@ -95,6 +97,7 @@ struct FrameDev {
 //   hits      2 records per hit (FP32: float4 pairs; FP64: 4 double2), at
 //             frames[f].hit_base + h:  (origin xyz, pixel)  (normal xyz, object id)
 //   vis       escaped AO samples per hit slot
+//   lmask     per hit slot, bit l set when the shadow ray toward light l escaped
 //   queue     [0] next primary work item, [1] next AO ray, [2] next shading item
 struct BatchDev {
     const FrameDev* frames;
@@ -104,6 +107,7 @@ struct BatchDev {
     unsigned long long* hit_off;
     void* hits;
     unsigned int* vis;
+    unsigned int* lmask;
     unsigned long long* queue;
     unsigned int* err;
     int32_t nframes;

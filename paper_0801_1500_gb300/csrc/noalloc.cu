@@ -15,13 +15,15 @@ namespace {
 //   counters   queue[4] (u64), job_off[2], hit_off[2] (u64), hit_count[1] (u32), err (u32)
 //   desc       one FrameDev, then tile_off[2] (i64)
 //   vis        GBRT_NOALLOC_MAX_PIXELS x u32
+//   lmask      GBRT_NOALLOC_MAX_PIXELS x u32 (shadow-ray light bits)
 //   hits       GBRT_NOALLOC_MAX_PIXELS x 64 B (large enough for FP64 records)
 constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 constexpr size_t OFF_COUNTERS = 0;
 constexpr size_t OFF_DESC = 256;
 constexpr size_t OFF_TILES = OFF_DESC + align256(sizeof(FrameDev));
 constexpr size_t OFF_VIS = OFF_TILES + 256;
-constexpr size_t OFF_HITS = OFF_VIS + align256((size_t)GBRT_NOALLOC_MAX_PIXELS * sizeof(uint32_t));
+constexpr size_t OFF_LMASK = OFF_VIS + align256((size_t)GBRT_NOALLOC_MAX_PIXELS * sizeof(uint32_t));
+constexpr size_t OFF_HITS = OFF_LMASK + align256((size_t)GBRT_NOALLOC_MAX_PIXELS * sizeof(uint32_t));
 constexpr size_t SCRATCH_BYTES = OFF_HITS + (size_t)GBRT_NOALLOC_MAX_PIXELS * 64;
 
 // Every GPU that loads the library holds this array until the process exits.
@@ -111,6 +113,7 @@ extern "C" GBRT_API int gbrt_render_noalloc(const gbrt_scene* scene, const gbrt_
         bd.err = (unsigned int*)(q + 8) + 1;
         bd.hits = base + OFF_HITS;
         bd.vis = (unsigned int*)(base + OFF_VIS);
+        bd.lmask = (unsigned int*)(base + OFF_LMASK);
         bd.nframes = 1;
         bd.tile_w = tw;
         bd.tile_h = th;

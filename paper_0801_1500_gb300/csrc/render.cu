@@ -251,6 +251,7 @@ __global__ void __launch_bounds__(256) k_primary(const __grid_constant__ BatchDe
                 HitIO<R>::store(b.hits, slot, madd(p, F.eps, n), n, q | (inside_hit ? HIT_INSIDE : 0u), id);
             }
             b.vis[slot] = 0u;
+            b.lmask[slot] = 0u;
             if (F.out_ids) F.out_ids[q] = id;
         } else {
             if (MODE == GBRT_FP32) {
@@ -280,7 +281,7 @@ __global__ void k_ao_plan(const __grid_constant__ BatchDev b) {
     for (int f = 0; f < b.nframes; ++f) {
         unsigned long long h = b.hit_count[f];
         hits += h;
-        jobs += h * (unsigned long long)b.frames[f].spp;
+        jobs += h * (unsigned long long)b.frames[f].jobs_per_hit;
         b.hit_off[f + 1] = hits;
         b.job_off[f + 1] = jobs;
     }
@@ -350,6 +351,7 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
     bool has = false, fresh = false, exhausted = false, overflow = false;
     Walk<R> w;
     uint32_t k = 0, e = 0;
+    uint32_t lbit = 0;  // 0: an AO sample; 1 << l: the shadow ray toward light l
     int64_t vslot = 0;
     const uint2* cells = nullptr;
     while (true) {
@@ -367,9 +369,9 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
                     const int f = find_frame(b.job_off, b.nframes, jj);
                     const FrameDev& F = b.frames[f];
                     const unsigned long long jl = jj - b.job_off[f];
-                    const uint32_t spp = (uint32_t)F.spp;
-                    const uint32_t h = jl < 0xFFFFFFFFull ? (uint32_t)jl / spp : (uint32_t)(jl / spp);
-                    const uint32_t smp = (uint32_t)(jl - (unsigned long long)h * spp);
+                    const uint32_t jph = (uint32_t)F.jobs_per_hit;
+                    const uint32_t h = jl < 0xFFFFFFFFull ? (uint32_t)jl / jph : (uint32_t)(jl / jph);
+                    const uint32_t smp = (uint32_t)(jl - (unsigned long long)h * jph);
                     vslot = F.hit_base + h;
                     V3<R> o, n;
                     uint32_t q, self;
@@ -377,11 +379,26 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
                     // the own object can be skipped only behind a convex outer side
                     if (q & HIT_INSIDE) self = GBRT_MISS;
                     q &= ~HIT_INSIDE;
-                    uint32_t b1, b2;
-                    ao_uniforms(q, smp, F.frame, F.seed_lo, F.seed_hi, b1, b2);
-                    const V3<R> d = cosine_dir(n, b1, b2);
-                    const R tmax = ao_maxdist<R>(F);
-                    if (walk_start(F.grid, o, d, R(0), tmax, w)) {
+                    V3<R> d;
+                    R tmax;
+                    bool cast = true;
+                    if (smp < (uint32_t)F.spp) {
+                        uint32_t b1, b2;
+                        ao_uniforms(q, smp, F.frame, F.seed_lo, F.seed_hi, b1, b2);
+                        d = cosine_dir(n, b1, b2);
+                        tmax = ao_maxdist<R>(F);
+                        lbit = 0u;
+                    } else {
+                        // shadow ray toward light l (none where the surface faces away)
+                        const int l = (int)(smp - (uint32_t)F.spp);
+                        d = ShadeP<R>::ldir(F, l);
+                        tmax = Num<R>::inf();
+                        lbit = 1u << l;
+                        cast = dot(n, d) > R(0);
+                    }
+                    if (!cast) {
+                        // the light cannot reach this side: its bit stays clear
+                    } else if (walk_start(F.grid, o, d, R(0), tmax, w)) {
                         cells = F.grid.cells;
                         AoRay<R> ray;
                         ray.o = o;
@@ -399,8 +416,10 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
                         e = cr.x + cr.y;
                         has = true;
                         fresh = true;
+                    } else if (lbit) {
+                        atomicOr(b.lmask + vslot, lbit);  // misses the objects' bounds: escapes
                     } else {
-                        atomicAdd(b.vis + vslot, 1u);  // misses the objects' bounds: escapes
+                        atomicAdd(b.vis + vslot, 1u);
                     }
                 }
             }
@@ -413,7 +432,9 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
                 k = cr.x;
                 e = cr.x + cr.y;
             } else {
-                atomicAdd(b.vis + vslot, 1u);  // walked out: escapes
+                // walked out: escapes
+                if (lbit) atomicOr(b.lmask + vslot, lbit);
+                else atomicAdd(b.vis + vslot, 1u);
                 has = false;
             }
         }
@@ -502,8 +523,9 @@ __global__ void __launch_bounds__(256) k_shade(const __grid_constant__ BatchDev 
             d = v3((R)d64.x, (R)d64.y, (R)d64.z);
         }
         R V = F.spp > 0 ? (R)vis / (R)F.spp : R(1);
+        const uint32_t lit = F.shadows ? b.lmask[slot] : 0xFFFFFFFFu;
         R rgb[3];
-        shade<R>(F, id, n, d, V, rgb);
+        shade<R>(F, id, n, d, V, lit, rgb);
         R* out = (R*)F.out_rgb + 3 * (size_t)q;
         out[0] = rgb[0];
         out[1] = rgb[1];
@@ -658,6 +680,8 @@ int render_frames(Ctx* ctx, FrameDev* frames, int n, bool use_graph) {
     int rc;
     if ((rc = grow(ctx, &ctx->d_hits, &ctx->hits_cap, (size_t)px * rec)) != GBRT_OK) return rc;
     if ((rc = grow(ctx, (void**)&ctx->d_vis, &ctx->vis_cap, (size_t)px * sizeof(unsigned))) != GBRT_OK) return rc;
+    if ((rc = grow(ctx, (void**)&ctx->d_lmask, &ctx->lmask_cap, (size_t)px * sizeof(unsigned))) != GBRT_OK)
+        return rc;
     if ((rc = grow(ctx, &ctx->d_desc, &ctx->desc_cap, desc_bytes)) != GBRT_OK) return rc;
     if ((rc = grow(ctx, &ctx->d_counters, &ctx->counters_cap, counters_bytes)) != GBRT_OK) return rc;
     if (ctx->h_desc_cap < desc_bytes) {
@@ -686,6 +710,7 @@ int render_frames(Ctx* ctx, FrameDev* frames, int n, bool use_graph) {
     bd.hit_count = (unsigned*)(bd.hit_off + (n + 1));
     bd.hits = ctx->d_hits;
     bd.vis = ctx->d_vis;
+    bd.lmask = ctx->d_lmask;
     bd.err = ctx->d_err;
     bd.nframes = n;
     bd.tile_w = tw;

@@ -43,7 +43,7 @@ class gbrt_lights(C.Structure):
 
 class gbrt_params(C.Structure):
     _fields_ = [("precision", C.c_int32), ("out_flags", C.c_int32), ("seed", C.c_uint64), ("frame", C.c_uint32),
-                ("reserved", C.c_uint32), ("eps", C.c_double), ("ao_maxdist", C.c_double), ("k_ao", C.c_double),
+                ("shadows", C.c_int32), ("eps", C.c_double), ("ao_maxdist", C.c_double), ("k_ao", C.c_double),
                 ("k_d", C.c_double), ("k_s", C.c_double), ("phong_exp", C.c_double),
                 ("background", C.c_double * 3)]
 
@@ -154,6 +154,7 @@ def make_params(p, precision=None, out_flags=0) -> gbrt_params:
     q.out_flags = int(out_flags)
     q.seed = int(p.seed)
     q.frame = int(p.frame)
+    q.shadows = 1 if getattr(p, "shadows", False) else 0
     q.eps = float(p.eps)
     q.ao_maxdist = float(p.ao_maxdist)
     q.k_ao, q.k_d, q.k_s, q.phong_exp = float(p.k_ao), float(p.k_d), float(p.k_s), float(p.phong_exp)

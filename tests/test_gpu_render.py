@@ -282,3 +282,29 @@ def test_pinhole_camera_inside_an_atom(G, R, oracle, prec):
     st = compare(rgb, ids, vis, ref)
     assert st["id_mismatch"] == 0 and st["frac_bad"] <= 1.0 / (W * H), st
     R.free(scene, grid)
+
+
+@pytest.mark.parametrize("prec", [S.PRECISION_FP32, S.PRECISION_FP64])
+def test_direct_light_shadows_small(G, R, oracle, prec):
+    w = S.small_fp64()
+    p = S.Params(ao_samples=8, seed=0, precision=prec, shadows=True)
+    scene, grid = R.upload(w.scene, lam=2.0)
+    rgb, ids, vis = gpu_frame(G, R, scene, grid, w.camera, w.width, w.height, w.lights, p)
+    ref = oracle.render(w.scene, w.camera, w.width, w.height, w.lights, p, mode="brute")
+    st = compare(rgb, ids, vis, ref)
+    assert_parity(st, "shadows small")
+    # shadows change the image
+    p0 = S.Params(ao_samples=8, seed=0, precision=prec, shadows=False)
+    rgb0, _, _ = gpu_frame(G, R, scene, grid, w.camera, w.width, w.height, w.lights, p0)
+    assert (np.abs(rgb0 - rgb).max(axis=1) > 1e-3).mean() > 0.05
+    R.free(scene, grid)
+
+
+def test_direct_light_shadows_paper_scene(G, R, oracle, paper):
+    w, scene, grid = paper
+    p = S.Params(ao_samples=16, seed=0, precision=S.PRECISION_FP32, shadows=True)
+    rgb, ids, vis = gpu_frame(G, R, scene, grid, w.camera, w.width, w.height, w.lights, p)
+    ref = oracle.render(w.scene, w.camera, w.width, w.height, w.lights, p, mode="grid", lam=2.0)
+    st = compare(rgb, ids, vis, ref)
+    print("paper 1.1MP shadows", st)
+    assert_parity(st, "shadows paper")
