@@ -503,9 +503,16 @@ def main():
     # side measurements on the same GPU: the plain FP64 path and 17.6 MP
     extras = {}
     if not args.no_extras and not orbit and args.workload == "paper_1mp":
-        for name, wk in (("fp64_path_1.1MP", S.paper_1mp(precision=S.PRECISION_FP64 if p.precision == S.PRECISION_FP32
-                                                         else S.PRECISION_FP32, scene=w.scene)),
-                         ("fp32_path_17.6MP", S.paper_17mp(precision=S.PRECISION_FP32, scene=w.scene))):
+        other = S.PRECISION_FP64 if p.precision == S.PRECISION_FP32 else S.PRECISION_FP32
+        mid = S.Workload("paper_26318obj_1930x2274_spp16", w.scene, 1930, 2274, S.Params(ao_samples=16),
+                         w.lights, S.ortho_camera(w.scene, 1930, 2274))
+        shadowed = S.paper_1mp(scene=w.scene)
+        shadowed.params.shadows = True
+        side = (("fp64_path_1.1MP", S.paper_1mp(precision=other, scene=w.scene), 3),
+                ("fp32_path_1.1MP_direct_light_shadows", shadowed, 5),
+                ("fp32_path_4.4MP", mid, 3),
+                ("fp32_path_17.6MP", S.paper_17mp(precision=S.PRECISION_FP32, scene=w.scene), 3))
+        for name, wk, nsteps in side:
             o2 = torch.empty((wk.height, wk.width, 3),
                              dtype=torch.float64 if wk.params.precision == S.PRECISION_FP64 else torch.float32,
                              device=dev)
@@ -514,14 +521,20 @@ def main():
             G.gbrt_render(r.ctx, scene, grid, c2, wk.width, wk.height, 16, l2, p2, o2, i2)
             G.gbrt_sync(r.ctx)
             h2 = int((i2.cpu().numpy().view(np.uint32) != G.MISS).sum())
+            # rays counted: primary + AO samples of hit pixels (shadow rays, at most one per
+            # light per hit, are not counted: Mrays/s of the shadow run is a lower bound)
             rays2 = wk.width * wk.height + 16 * h2
             ms2, _ = time_steps(torch, stream, flush,
                                 lambda: G.gbrt_render(r.ctx, scene, grid, c2, wk.width, wk.height, 16, l2, p2, o2),
-                                3, 2)
+                                nsteps, 2)
             m2 = sum(ms2) / len(ms2)
             extras[name] = {"Mrays_s": round(rays2 / m2 / 1e3, 2), "ms_per_frame": round(m2, 4),
                             "fps": round(1e3 / m2, 2), "rays_per_frame": rays2,
                             "dtype": "f64" if wk.params.precision == S.PRECISION_FP64 else "f32"}
+        # weak-scaling analogue of the paper's Table 4 (1.1 / 4.4 / 17.6 MP), on one GPU
+        extras["resolution_sweep_Mrays_s"] = {"1.1MP": round(value, 1),
+                                              "4.4MP": extras["fp32_path_4.4MP"]["Mrays_s"],
+                                              "17.6MP": extras["fp32_path_17.6MP"]["Mrays_s"]}
 
     cpu = None
     roof = None
