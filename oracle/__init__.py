@@ -181,8 +181,9 @@ def ao_probe(scene, pts, nrm, spp, seed=0, frame=0, eps=1e-3, maxdist=math.inf, 
 
 
 def camera_vector(cam):
-    """Flatten a camera object: kind, eye, dir, up, right, half_w, half_h."""
-    v = np.zeros(15)
+    """Flatten a camera object: kind, eye, dir, up, right, half_w, half_h,
+    sub-pixel grid side m (``aa``, default 1)."""
+    v = np.zeros(16)
     v[0] = float(cam.kind)
     v[1:4] = cam.eye
     v[4:7] = cam.dir
@@ -190,6 +191,7 @@ def camera_vector(cam):
     v[10:13] = cam.right
     v[13] = cam.half_w
     v[14] = cam.half_h
+    v[15] = float(max(1, int(getattr(cam, "aa", 1) or 1)))
     return v
 
 
@@ -216,8 +218,11 @@ def render(scene, camera, width, height, lights, params, pixels=None, mode="grid
            spp=None):
     """Render the listed pixel indices (j*W + i), or the whole frame.
 
-    Returns a dict with rgb [n,3] float64, id [n] uint32 (0xFFFFFFFF = miss),
-    t [n], vis [n] (unoccluded AO samples), grazing [n] bool, counters dict.
+    Returns a dict with rgb [n,3] float64 per pixel and, per sub-sample
+    (n m^2 entries, pixel-major, then sub-row b, then sub-column a; m = the
+    camera's sub-pixel grid side, 1 without supersampling): id uint32
+    (0xFFFFFFFF = miss), t, vis (unoccluded AO samples), grazing bool; and a
+    counters dict.
     """
     sph, cyl, col, pal = _scene_arrays(scene)
     cam = camera_vector(camera)
@@ -231,11 +236,12 @@ def render(scene, camera, width, height, lights, params, pixels=None, mode="grid
     else:
         pix = np.ascontiguousarray(np.asarray(pixels, np.int64))
         npix = pix.shape[0]
+    nsub = npix * int(cam[15]) ** 2
     rgb = np.zeros((npix, 3))
-    ids = np.zeros(npix, np.uint32)
-    ts = np.zeros(npix)
-    vis = np.zeros(npix, np.int32)
-    gz = np.zeros(npix, np.uint8)
+    ids = np.zeros(nsub, np.uint32)
+    ts = np.zeros(nsub)
+    vis = np.zeros(nsub, np.int32)
+    gz = np.zeros(nsub, np.uint8)
     cnt = np.zeros(16, np.int64)
     rc = lib().oracle_render(sph.shape[0], _p(sph), cyl.shape[0], _p(cyl), _p(col), _p(pal), pal.shape[0],
                              _p(cam), int(width), int(height), _p(ldir), _p(lI), ldir.shape[0], _p(sp),

@@ -567,13 +567,16 @@ static void refine(const oscene* sc, uint32_t id, const double o[3], const doubl
 /* ------------------------------------------------------------------------ */
 /* Camera                                                                    */
 /*  cam[0] kind (0 ortho, 1 pinhole), cam[1..3] eye, [4..6] dir, [7..9] up,  */
-/*  [10..12] right, [13] half_w, [14] half_h                                  */
+/*  [10..12] right, [13] half_w, [14] half_h, [15] m: sub-pixel grid side     */
+/*  (supersampling; 0 or 1 = one ray through the pixel centre)                */
+/* The ray passes through the image-plane point (x, y) in pixel units,       */
+/* x across from the left edge, y down from the top edge.                     */
 /* ------------------------------------------------------------------------ */
 
-static void primary_ray(const double* cam, int W, int H, int64_t i, int64_t j, double o[3], double d[3])
+static void primary_ray(const double* cam, int W, int H, double x, double y, double o[3], double d[3])
 {
-    double u = cam[13] * (2.0 * ((double)i + 0.5) / W - 1.0);
-    double v = cam[14] * (1.0 - 2.0 * ((double)j + 0.5) / H);
+    double u = cam[13] * (2.0 * x / W - 1.0);
+    double v = cam[14] * (1.0 - 2.0 * y / H);
     if (cam[0] == 0.0) {
         for (int k = 0; k < 3; ++k) { o[k] = cam[1 + k] + u * cam[10 + k] + v * cam[7 + k]; d[k] = cam[4 + k]; }
     } else {
@@ -755,10 +758,16 @@ int oracle_ao_probe(int64_t S, const double* sph, int64_t C, const double* cyl, 
 
 /*
  * Render the listed pixels (pix[k] = j*W + i; pix == NULL -> all W*H in order).
- * Per pixel: primary ray through the pixel centre -> nearest hit -> refined hit
- * point and normal -> `spp` AO rays from p + eps n -> shade.
- * Outputs per listed pixel (any may be NULL): rgb (3 doubles), hit id
- * (0xFFFFFFFF = miss), hit t, number of unoccluded AO samples, grazing flag.
+ * Per pixel and per sub-sample (a, b) of its m x m regular sub-pixel grid
+ * (m = cam[15]; m = 1: the pixel centre only): primary ray through the point
+ * (i + (a + 0.5)/m, j + (b + 0.5)/m) -> nearest hit -> refined hit point and
+ * normal -> `spp` AO rays from p + eps n -> shade -> clamp. The pixel's colour
+ * is the mean of its m^2 sub-sample colours (a box filter). The AO samples of
+ * sub-sample (a, b) use Philox counter word 0 = its index in the m-times finer
+ * raster, (m j + b) (m W) + (m i + a), which is the pixel index when m = 1.
+ * Outputs (any may be NULL): rgb (3 doubles) per listed pixel; hit id
+ * (0xFFFFFFFF = miss), hit t, number of unoccluded AO samples and grazing flag
+ * per sub-sample, at [k m^2 + b m + a].
  * counters[16] (may be NULL): 0 primary rays, 1 AO rays, 2 hit pixels,
  *   3 primary cells, 4 primary sphere tests, 5 primary cylinder tests,
  *   6 AO cells, 7 AO sphere tests, 8 AO cylinder tests, 9 unoccluded AO rays.
@@ -774,6 +783,8 @@ int oracle_render(int64_t S, const double* sph, int64_t C, const double* cyl,
                   int64_t* counters, int32_t nthreads)
 {
     if (W <= 0 || H <= 0) return -2;
+    const int m = cam[15] >= 1.0 ? (int)cam[15] : 1;
+    if (m > 16) return -2;
     oworld w;
     if (world_init(&w, S, sph, C, cyl, color, palette, K, mode, lambda)) return -1;
     if (!pix) npix = (int64_t)W * H;
@@ -792,48 +803,60 @@ int oracle_render(int64_t S, const double* sph, int64_t C, const double* cyl,
         for (int64_t k = 0; k < npix; ++k) {
             int64_t q = pix ? pix[k] : k;
             int64_t i = q % W, j = q / W;
-            double o[3], d[3];
-            primary_ray(cam, W, H, i, j, o, d);
-            nearest_t nr;
-            ocount pc = {0, 0, 0}, ac = {0, 0, 0};
-            world_nearest(&w, o, d, 0.0, INFINITY, &nr, &pc);
-            loc[0]++;
-            loc[3] += pc.cells; loc[4] += pc.sph; loc[5] += pc.cyl;
-            double rgb[3] = {sp[8], sp[9], sp[10]};
-            int32_t vis = 0;
-            if (nr.id1 != OR_MISS) {
-                loc[2]++;
-                double p[3], n[3];
-                refine(&w.sc, nr.id1, o, d, nr.t1, p, n);
-                double ao_o[3] = {p[0] + sp[6] * n[0], p[1] + sp[6] * n[1], p[2] + sp[6] * n[2]};
-                for (int s = 0; s < spp; ++s) {
-                    double u1, u2, dir[3];
-                    oracle_ao_uniforms((uint32_t)q, (uint32_t)s, frame, seed, &u1, &u2);
-                    oracle_cosine_dir(n, u1, u2, dir);
-                    if (!world_anyhit(&w, ao_o, dir, sp[7], &ac)) vis++;
-                }
-                loc[1] += spp;
-                loc[6] += ac.cells; loc[7] += ac.sph; loc[8] += ac.cyl; loc[9] += vis;
-                double V = spp > 0 ? (double)vis / spp : 1.0;
-                /* direct-light shadow rays: from the AO origin toward each light
-                 * the surface faces; any hit (0 < t) blocks that light */
-                int lit[64];
-                for (int l = 0; l < nl && l < 64; ++l) {
-                    lit[l] = 1;
-                    if (sp[11] != 0.0 && dot3(n, ldir + 3 * l) > 0.0) {
-                        ocount sc_ = {0, 0, 0};
-                        lit[l] = !world_anyhit(&w, ao_o, ldir + 3 * l, INFINITY, &sc_);
+            double acc[3] = {0.0, 0.0, 0.0};
+            for (int b = 0; b < m; ++b) {
+                for (int a = 0; a < m; ++a) {
+                    const int64_t sub = k * m * m + b * m + a;
+                    /* counter word 0: the sub-sample's index in the finer raster */
+                    const uint32_t qf = (uint32_t)(((int64_t)m * j + b) * ((int64_t)m * W) + ((int64_t)m * i + a));
+                    double o[3], d[3];
+                    primary_ray(cam, W, H, (double)i + (a + 0.5) / m, (double)j + (b + 0.5) / m, o, d);
+                    nearest_t nr;
+                    ocount pc = {0, 0, 0}, ac = {0, 0, 0};
+                    world_nearest(&w, o, d, 0.0, INFINITY, &nr, &pc);
+                    loc[0]++;
+                    loc[3] += pc.cells; loc[4] += pc.sph; loc[5] += pc.cyl;
+                    double rgb[3] = {sp[8], sp[9], sp[10]};
+                    int32_t vis = 0;
+                    if (nr.id1 != OR_MISS) {
+                        loc[2]++;
+                        double p[3], n[3];
+                        refine(&w.sc, nr.id1, o, d, nr.t1, p, n);
+                        double ao_o[3] = {p[0] + sp[6] * n[0], p[1] + sp[6] * n[1], p[2] + sp[6] * n[2]};
+                        for (int s = 0; s < spp; ++s) {
+                            double u1, u2, dir[3];
+                            oracle_ao_uniforms(qf, (uint32_t)s, frame, seed, &u1, &u2);
+                            oracle_cosine_dir(n, u1, u2, dir);
+                            if (!world_anyhit(&w, ao_o, dir, sp[7], &ac)) vis++;
+                        }
+                        loc[1] += spp;
+                        loc[6] += ac.cells; loc[7] += ac.sph; loc[8] += ac.cyl; loc[9] += vis;
+                        double V = spp > 0 ? (double)vis / spp : 1.0;
+                        /* direct-light shadow rays: from the AO origin toward each light
+                         * the surface faces; any hit (0 < t) blocks that light */
+                        int lit[64];
+                        for (int l = 0; l < nl && l < 64; ++l) {
+                            lit[l] = 1;
+                            if (sp[11] != 0.0 && dot3(n, ldir + 3 * l) > 0.0) {
+                                ocount sc_ = {0, 0, 0};
+                                lit[l] = !world_anyhit(&w, ao_o, ldir + 3 * l, INFINITY, &sc_);
+                            }
+                        }
+                        uint32_t ci = w.sc.color[nr.id1];
+                        double albedo[3] = {palette[3 * ci], palette[3 * ci + 1], palette[3 * ci + 2]};
+                        shade(albedo, n, d, V, ldir, lI, nl, sp, lit, rgb);
                     }
+                    acc[0] += rgb[0]; acc[1] += rgb[1]; acc[2] += rgb[2];
+                    if (out_id) out_id[sub] = nr.id1;
+                    if (out_t) out_t[sub] = nr.id1 == OR_MISS ? INFINITY : nr.t1;
+                    if (out_vis) out_vis[sub] = vis;
+                    if (out_grazing) out_grazing[sub] = (uint8_t)is_grazing(&nr);
                 }
-                uint32_t ci = w.sc.color[nr.id1];
-                double albedo[3] = {palette[3 * ci], palette[3 * ci + 1], palette[3 * ci + 2]};
-                shade(albedo, n, d, V, ldir, lI, nl, sp, lit, rgb);
             }
-            if (out_rgb) { out_rgb[3 * k] = rgb[0]; out_rgb[3 * k + 1] = rgb[1]; out_rgb[3 * k + 2] = rgb[2]; }
-            if (out_id) out_id[k] = nr.id1;
-            if (out_t) out_t[k] = nr.id1 == OR_MISS ? INFINITY : nr.t1;
-            if (out_vis) out_vis[k] = vis;
-            if (out_grazing) out_grazing[k] = (uint8_t)is_grazing(&nr);
+            if (out_rgb) {
+                const double mm = (double)m * m;
+                out_rgb[3 * k] = acc[0] / mm; out_rgb[3 * k + 1] = acc[1] / mm; out_rgb[3 * k + 2] = acc[2] / mm;
+            }
         }
 #ifdef _OPENMP
 #pragma omp critical

@@ -184,6 +184,9 @@ class Camera:
       u = half_w * (2 (i + 0.5) / W - 1),  v = half_h * (1 - 2 (j + 0.5) / H).
     Pinhole: origin = eye, direction = normalize(dir + u*right + v*up) with the
       same u, v (half_w, half_h are then the tangents of the half angles).
+    Supersampling (aa = m > 1): each pixel casts m x m rays through the points
+      (i + (a + 0.5)/m, j + (b + 0.5)/m), a, b = 0..m-1, in place of the centre
+      (i + 0.5, j + 0.5), and its colour is the mean of theirs.
     """
 
     eye: tuple
@@ -193,6 +196,7 @@ class Camera:
     half_w: float
     half_h: float
     kind: int = CAMERA_ORTHO
+    aa: int = 1
 
 
 def ortho_camera(scene: Scene, width: int, height: int, angle_deg: float = 0.0,
@@ -222,6 +226,29 @@ def ortho_camera(scene: Scene, width: int, height: int, angle_deg: float = 0.0,
     return Camera(eye=tuple(float(x) for x in eye), dir=tuple(float(x) for x in -back),
                   up=(0.0, 1.0, 0.0), right=tuple(float(x) for x in right),
                   half_w=float(hw), half_h=float(hh), kind=CAMERA_ORTHO)
+
+
+def pinhole_camera(scene: Scene, width: int, height: int, angle_deg: float = 0.0, fov_deg: float = 40.0,
+                   margin: float = 1.05, aa: int = 1) -> Camera:
+    """Pinhole view of the scene down -z, rotated by ``angle_deg`` about +y.
+
+    The vertical field of view is ``fov_deg``; the eye sits on the view axis
+    through the box centre, far enough that the box's bounding sphere (times
+    ``margin``) fits the vertical field. ``aa`` is the sub-pixel grid side.
+    """
+    lo, hi = scene.bounds()
+    ctr = 0.5 * (lo + hi)
+    rad = max(0.5 * float(np.linalg.norm(hi - lo)), 1e-6) * margin
+    hh = math.tan(math.radians(fov_deg) / 2.0)
+    hw = hh * width / float(height)
+    dist = rad / math.sin(math.radians(fov_deg) / 2.0)
+    th = math.radians(angle_deg)
+    back = np.array([math.sin(th), 0.0, math.cos(th)])
+    right = np.array([math.cos(th), 0.0, -math.sin(th)])
+    eye = ctr + dist * back
+    return Camera(eye=tuple(float(x) for x in eye), dir=tuple(float(x) for x in -back),
+                  up=(0.0, 1.0, 0.0), right=tuple(float(x) for x in right),
+                  half_w=float(hw), half_h=float(hh), kind=CAMERA_PINHOLE, aa=int(aa))
 
 
 def _norm(v):
