@@ -508,22 +508,26 @@ def main():
                          w.lights, S.ortho_camera(w.scene, 1930, 2274))
         shadowed = S.paper_1mp(scene=w.scene)
         shadowed.params.shadows = True
+        pin_aa = S.Workload("paper_26318obj_965x1137_pinhole_aa2x2_spp16", w.scene, W, H, S.Params(ao_samples=16),
+                            w.lights, S.pinhole_camera(w.scene, W, H, 30.0, aa=2))
         side = (("fp64_path_1.1MP", S.paper_1mp(precision=other, scene=w.scene), 3),
                 ("fp32_path_1.1MP_direct_light_shadows", shadowed, 5),
+                ("fp32_path_1.1MP_pinhole_2x2_supersampled", pin_aa, 3),
                 ("fp32_path_4.4MP", mid, 3),
                 ("fp32_path_17.6MP", S.paper_17mp(precision=S.PRECISION_FP32, scene=w.scene), 3))
         for name, wk, nsteps in side:
             o2 = torch.empty((wk.height, wk.width, 3),
                              dtype=torch.float64 if wk.params.precision == S.PRECISION_FP64 else torch.float32,
                              device=dev)
-            i2 = torch.empty((wk.height, wk.width), dtype=torch.int32, device=dev)
+            aa2 = max(1, wk.camera.aa)  # hit ids per sub-sample
+            i2 = torch.empty((aa2 * wk.height, aa2 * wk.width), dtype=torch.int32, device=dev)
             c2, l2, p2 = G.make_camera(wk.camera), G.make_lights(wk.lights), G.make_params(wk.params)
             G.gbrt_render(r.ctx, scene, grid, c2, wk.width, wk.height, 16, l2, p2, o2, i2)
             G.gbrt_sync(r.ctx)
             h2 = int((i2.cpu().numpy().view(np.uint32) != G.MISS).sum())
             # rays counted: primary + AO samples of hit pixels (shadow rays, at most one per
             # light per hit, are not counted: Mrays/s of the shadow run is a lower bound)
-            rays2 = wk.width * wk.height + 16 * h2
+            rays2 = aa2 * aa2 * wk.width * wk.height + 16 * h2
             ms2, _ = time_steps(torch, stream, flush,
                                 lambda: G.gbrt_render(r.ctx, scene, grid, c2, wk.width, wk.height, 16, l2, p2, o2),
                                 nsteps, 2)

@@ -41,7 +41,7 @@ extern "C" {
 #define GBRT_API
 #endif
 
-#define GBRT_VERSION 2
+#define GBRT_VERSION 3
 
 /* ---- error codes ---- */
 #define GBRT_OK 0
@@ -67,6 +67,7 @@ extern "C" {
 #define GBRT_MAX_SAMPLES 4096    /* ao_samples bound of a render */
 #define GBRT_MAX_PROBE_SAMPLES (1 << 20) /* ao_samples bound of gbrt_ao_probe */
 #define GBRT_MAX_DIM 65536       /* width/height bound; width*height < 2^31 */
+#define GBRT_MAX_AA 4            /* largest sub-pixel grid side (camera.aa) */
 
 typedef struct gbrt_ctx gbrt_ctx;
 typedef struct gbrt_scene gbrt_scene;
@@ -76,10 +77,18 @@ typedef struct gbrt_grid gbrt_grid;
  *   u = half_w (2 (i + 0.5)/W - 1),  v = half_h (1 - 2 (j + 0.5)/H).
  * Ortho: ray origin eye + u right + v up, direction dir.
  * Pinhole: origin eye, direction normalize(dir + u right + v up).
- * dir, up, right: unit and mutually orthogonal. */
+ * dir, up, right: unit and mutually orthogonal.
+ * aa: supersampling, an addition to the paper's one ray per pixel. 0 or 1:
+ *   one ray through the pixel centre. m = 2..GBRT_MAX_AA: m x m rays through
+ *   (i + (a + 0.5)/m, j + (b + 0.5)/m), a, b = 0..m-1 -- the pixel centres of
+ *   the m-times finer raster of (m W) x (m H) pixels -- and the pixel's colour
+ *   is the mean of their (clamped) colours. Sub-sample (a, b) draws its AO
+ *   samples with counter word 0 = its finer-raster index
+ *   (m j + b) (m W) + (m i + a); hit ids and AO counts are reported per
+ *   sub-sample in that finer raster. (m W) (m H) must stay below 2^31. */
 typedef struct gbrt_camera {
     int32_t kind;
-    int32_t reserved;
+    int32_t aa;
     double eye[3];
     double dir[3];
     double up[3];
@@ -239,6 +248,10 @@ GBRT_API int gbrt_grid_free(gbrt_ctx* ctx, gbrt_grid* grid);
  *  out_rgb         [height][width][3], float32 for GBRT_FP32, float64 for GBRT_FP64
  *  out_hit_ids     optional uint32 [height][width]: nearest object id, GBRT_MISS
  *  out_ao_visible  optional uint32 [height][width]: AO samples that escaped
+ * With supersampling (camera->aa = m > 1) out_hit_ids and out_ao_visible hold
+ * one entry per sub-sample, [m height][m width] (the finer raster), and the
+ * library keeps the finer raster's colours in a context buffer
+ * (m^2 width height x 3 values) that it box-filters into out_rgb.
  * Output pointers are device memory unless params->out_flags has
  * GBRT_HOST_PTRS, in which case the library renders into its own device
  * buffer, copies back and synchronises. Asynchronous otherwise. */
@@ -285,7 +298,8 @@ GBRT_API int gbrt_philox4x32_10(gbrt_ctx* ctx, const uint32_t* ctr, const uint32
  *
  *  - width * height must not exceed GBRT_NOALLOC_MAX_PIXELS (256 x 256);
  *    larger frames are rejected with GBRT_EINVAL, as are host output
- *    pointers (params->out_flags must be 0).
+ *    pointers (params->out_flags must be 0) and supersampling
+ *    (camera->aa > 1).
  *  - The first call on a device does that device's set-up (it looks up the
  *    array's device address and configures the kernels); make that first
  *    call before any stream capture.

@@ -22,6 +22,11 @@ int check_frame_args(const gbrt_scene* scene, const gbrt_grid* grid, const gbrt_
     if (W <= 0 || H <= 0 || W > GBRT_MAX_DIM || H > GBRT_MAX_DIM || (int64_t)W * H >= (1ll << 31)) return GBRT_EINVAL;
     if (spp < 0 || spp > GBRT_MAX_SAMPLES) return GBRT_EINVAL;
     if (cam->kind != GBRT_CAMERA_ORTHO && cam->kind != GBRT_CAMERA_PINHOLE) return GBRT_EINVAL;
+    if (cam->aa < 0 || cam->aa > GBRT_MAX_AA) return GBRT_EINVAL;
+    {
+        const int64_t m = cam->aa > 1 ? cam->aa : 1;
+        if (m * W * m * H >= (1ll << 31)) return GBRT_EINVAL;
+    }
     if (!finite3(cam->eye) || !finite3(cam->dir) || !finite3(cam->up) || !finite3(cam->right)) return GBRT_EINVAL;
     if (!(cam->half_w > 0) || !(cam->half_h > 0) || !std::isfinite(cam->half_w) || !std::isfinite(cam->half_h))
         return GBRT_EINVAL;
@@ -46,6 +51,12 @@ FrameDev make_frame(const gbrt_scene* scene, const gbrt_grid* grid, const gbrt_c
                     uint32_t* out_vis) {
     FrameDev f;
     memset(&f, 0, sizeof(f));
+    // supersampling renders the m-times finer raster (its pixel centres are
+    // the sub-sample points) and box-filters it afterwards
+    const int32_t m = cam->aa > 1 ? cam->aa : 1;
+    W *= m;
+    H *= m;
+    f.aa = m;
     f.scene = scene->view();
     f.grid = grid->dev;
     for (int k = 0; k < 3; ++k) {
@@ -108,6 +119,8 @@ FrameDev make_frame(const gbrt_scene* scene, const gbrt_grid* grid, const gbrt_c
         f.bg_f[k] = (float)p->background[k];
     }
     f.out_rgb = out_rgb;
+    f.out_final = out_rgb;
+    f.rgb_q0 = 0;
     f.out_ids = out_ids;
     f.out_vis = out_vis;
     return f;
@@ -251,6 +264,7 @@ GBRT_API int gbrt_destroy(gbrt_ctx* ctx) {
     cudaFree(ctx->d_hits);
     cudaFree(ctx->d_vis);
     cudaFree(ctx->d_lmask);
+    cudaFree(ctx->d_fine);
     cudaFree(ctx->d_desc);
     cudaFreeHost(ctx->h_desc);
     cudaFree(ctx->d_counters);
@@ -352,8 +366,10 @@ GBRT_API int gbrt_render(gbrt_ctx* ctx, const gbrt_scene* scene, const gbrt_grid
     DeviceGuard g(ctx->device);
     if (!g.ok) return GBRT_EDEVICE;
     const bool host = (params->out_flags & GBRT_HOST_PTRS) != 0;
-    const size_t npx = (size_t)width * (size_t)height;
-    const size_t rgb_bytes = npx * 3 * (params->precision == GBRT_FP64 ? sizeof(double) : sizeof(float));
+    const size_t aa = camera->aa > 1 ? (size_t)camera->aa : 1;
+    const size_t rgb_bytes =
+        (size_t)width * height * 3 * (params->precision == GBRT_FP64 ? sizeof(double) : sizeof(float));
+    const size_t npx = (size_t)width * height * aa * aa;  // hit ids and AO counts: one per sub-sample
     void* d_rgb = out_rgb;
     uint32_t* d_ids = out_hit_ids;
     uint32_t* d_vis = out_ao_visible;
@@ -409,8 +425,9 @@ GBRT_API int gbrt_render_batch(gbrt_ctx* ctx, const gbrt_render_item* items, int
             frames.push_back(make_frame(it.scene, it.grid, &it.camera, it.width, it.height, it.ao_samples,
                                         &it.lights, &it.params, it.out_rgb, it.out_hit_ids, it.out_ao_visible));
             if (it.row_end > 0) {
-                frames.back().row0 = it.row_begin;
-                frames.back().rows = it.row_end - it.row_begin;
+                const int32_t m = frames.back().aa;
+                frames.back().row0 = m * it.row_begin;
+                frames.back().rows = m * (it.row_end - it.row_begin);
             }
         }
         if (frames.empty()) continue;

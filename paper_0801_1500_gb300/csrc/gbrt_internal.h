@@ -29,6 +29,8 @@ struct Ctx {
     size_t vis_cap = 0;
     unsigned int* d_lmask = nullptr;
     size_t lmask_cap = 0;
+    void* d_fine = nullptr;  // finer-raster colours of supersampled frames
+    size_t fine_cap = 0;
     void* d_desc = nullptr;
     size_t desc_cap = 0;
     void* h_desc = nullptr;  // pinned staging of the descriptors
@@ -43,6 +45,7 @@ struct Ctx {
     cudaGraphExec_t graph_exec = nullptr;
     bool graph_valid = false;
     long long graph_key = 0;
+    bool graph_resolve = false;  // the captured graph ends with the supersampling resolve
     BatchDev graph_bd{};
     // per-kernel timing
     bool profiling = false;

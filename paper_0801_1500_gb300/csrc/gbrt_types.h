@@ -77,10 +77,17 @@ struct FrameDev {
     float ao_maxdist_f;
     double bg[3];
     float bg_f[3];
-    // outputs (device)
+    // outputs (device). Pixel q of the rendered raster writes its colour at
+    // out_rgb + 3 (q - rgb_q0). With supersampling (aa = m > 1) the rendered
+    // raster is the m-times finer one (W, H, row0, rows count its pixels),
+    // out_rgb is the library's buffer for the band's finer rows, and the
+    // resolve pass box-filters it into out_final ((W/m) x (H/m) pixels).
     void* out_rgb;
     uint32_t* out_ids;
     uint32_t* out_vis;
+    void* out_final;
+    int64_t rgb_q0;
+    int32_t aa;
     // rows [row0, row0 + rows) of the image are rendered (a band, or all rows);
     // their tiling into primary-ray work items (tile_w x tile_h = 32)
     int32_t row0, rows;

@@ -86,6 +86,7 @@ extern "C" GBRT_API int gbrt_render_noalloc(const gbrt_scene* scene, const gbrt_
     if (rc != GBRT_OK) return rc;
     if (params->out_flags != 0) return GBRT_EINVAL;  // outputs must be device memory
     if ((int64_t)width * height > GBRT_NOALLOC_MAX_PIXELS) return GBRT_EINVAL;
+    if (camera->aa > 1) return GBRT_EINVAL;  // supersampling needs a finer-raster buffer
     int prev = -1;
     if (cudaGetDevice(&prev) != cudaSuccess) return GBRT_EDEVICE;
     if (prev != scene->device && cudaSetDevice(scene->device) != cudaSuccess) return GBRT_EDEVICE;

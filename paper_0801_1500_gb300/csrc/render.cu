@@ -255,12 +255,12 @@ __global__ void __launch_bounds__(256) k_primary(const __grid_constant__ BatchDe
             if (F.out_ids) F.out_ids[q] = id;
         } else {
             if (MODE == GBRT_FP32) {
-                float* out = (float*)F.out_rgb + 3 * (size_t)q;
+                float* out = (float*)F.out_rgb + 3 * (size_t)(q - F.rgb_q0);
                 out[0] = F.bg_f[0];
                 out[1] = F.bg_f[1];
                 out[2] = F.bg_f[2];
             } else {
-                double* out = (double*)F.out_rgb + 3 * (size_t)q;
+                double* out = (double*)F.out_rgb + 3 * (size_t)(q - F.rgb_q0);
                 out[0] = F.bg[0];
                 out[1] = F.bg[1];
                 out[2] = F.bg[2];
@@ -526,11 +526,48 @@ __global__ void __launch_bounds__(256) k_shade(const __grid_constant__ BatchDev 
         const uint32_t lit = F.shadows ? b.lmask[slot] : 0xFFFFFFFFu;
         R rgb[3];
         shade<R>(F, id, n, d, V, lit, rgb);
-        R* out = (R*)F.out_rgb + 3 * (size_t)q;
+        R* out = (R*)F.out_rgb + 3 * (size_t)(q - F.rgb_q0);
         out[0] = rgb[0];
         out[1] = rgb[1];
         out[2] = rgb[2];
         if (F.out_vis) F.out_vis[q] = vis;
+    }
+}
+
+// ---------------------------------------------------------------- supersampling
+
+// Box filter of supersampled frames: output pixel (i, j) is the mean of the
+// m x m finer-raster colours (m i + a, m j + b), summed sub-row by sub-row.
+// Frames are strided over blockIdx.y; frames without supersampling are skipped.
+template <class R>
+__global__ void __launch_bounds__(256) k_resolve(const __grid_constant__ BatchDev b) {
+    for (int f = blockIdx.y; f < b.nframes; f += gridDim.y) {
+        const FrameDev& F = b.frames[f];
+        const int m = F.aa;
+        if (m <= 1) continue;
+        const int w = F.W / m;
+        const int j0 = F.row0 / m;
+        const long long n = (long long)w * (F.rows / m);
+        const R mm = (R)(m * m);
+        const R* fine = (const R*)F.out_rgb;
+        R* out = (R*)F.out_final;
+        for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+             k += (long long)gridDim.x * blockDim.x) {
+            const int i = (int)(k % w), j = j0 + (int)(k / w);
+            R acc[3] = {R(0), R(0), R(0)};
+            for (int sb = 0; sb < m; ++sb) {
+                const R* row = fine + 3 * ((long long)(m * j + sb) * F.W + (long long)m * i - F.rgb_q0);
+                for (int sa = 0; sa < m; ++sa) {
+                    acc[0] += row[3 * sa];
+                    acc[1] += row[3 * sa + 1];
+                    acc[2] += row[3 * sa + 2];
+                }
+            }
+            R* o = out + 3 * ((long long)j * w + i);
+            o[0] = acc[0] / mm;
+            o[1] = acc[1] / mm;
+            o[2] = acc[2] / mm;
+        }
     }
 }
 
@@ -595,7 +632,7 @@ int persistent_grid(Ctx* ctx, K kernel, int block, size_t smem = 0) {
 // Lay out one batch (all frames of one precision), upload its descriptors and
 // enqueue memsets + the four kernels on `stream`.
 struct Grids {
-    int primary, ao, shade;
+    int primary, ao, shade, resolve;
 };
 
 static Grids grids_for(Ctx* ctx, int precision) {
@@ -617,11 +654,12 @@ static Grids grids_for(Ctx* ctx, int precision) {
         g.ao = persistent_grid(ctx, k_ao_walk<double>, block, (block / 32) * sizeof(AoWarp<double>));
     }
     g.shade = ctx->num_sms * 8;
+    g.resolve = ctx->num_sms * 4;
     return g;
 }
 
 static int enqueue_batch(Ctx* ctx, cudaStream_t stream, int precision, const BatchDev& bd, size_t desc_bytes,
-                         const Grids& gr) {
+                         const Grids& gr, bool resolve) {
     cudaError_t e = cudaMemcpyAsync(ctx->d_desc, ctx->h_desc, desc_bytes, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_counters, 0, ctx->counters_bytes_used, stream);
     if (e != cudaSuccess) return err_of(e);
@@ -640,6 +678,7 @@ static int enqueue_batch(Ctx* ctx, cudaStream_t stream, int precision, const Bat
         k_ao_walk<float><<<gr.ao, block, (block / 32) * sizeof(AoWarp<float>), stream>>>(bd);
         mark(3);
         k_shade<float><<<gr.shade, 256, 0, stream>>>(bd);
+        if (resolve) k_resolve<float><<<dim3(gr.resolve, std::min(bd.nframes, 65535)), 256, 0, stream>>>(bd);
     } else {
         k_primary<GBRT_FP64><<<gr.primary, block, 0, stream>>>(bd);
         mark(1);
@@ -648,10 +687,11 @@ static int enqueue_batch(Ctx* ctx, cudaStream_t stream, int precision, const Bat
         k_ao_walk<double><<<gr.ao, block, (block / 32) * sizeof(AoWarp<double>), stream>>>(bd);
         mark(3);
         k_shade<double><<<gr.shade, 256, 0, stream>>>(bd);
+        if (resolve) k_resolve<double><<<dim3(gr.resolve, std::min(bd.nframes, 65535)), 256, 0, stream>>>(bd);
     }
     mark(4);
     if (tm) ctx->timed = true;
-    ctx->launches += 4;
+    ctx->launches += resolve ? 5 : 4;
     return err_of(cudaGetLastError());
 }
 
@@ -670,14 +710,31 @@ int render_frames(Ctx* ctx, FrameDev* frames, int n, bool use_graph) {
                                   2 * (size_t)(n + 1) * sizeof(unsigned long long) + 64;
     int64_t px = 0;
     long long tiles = 0;
+    size_t fine_bytes = 0;  // finer-raster colours of the supersampled frames' bands
+    bool resolve = false;
+    const size_t rgb_px = 3 * (precision == GBRT_FP32 ? sizeof(float) : sizeof(double));
     for (int f = 0; f < n; ++f) {
         frames[f].tiles_x = (frames[f].W + tw - 1) / tw;
         frames[f].tiles_y = (frames[f].rows + th - 1) / th;
         frames[f].hit_base = px;
         px += (int64_t)frames[f].W * frames[f].rows;
         tiles += (long long)frames[f].tiles_x * frames[f].tiles_y;
+        if (frames[f].aa > 1) {
+            resolve = true;
+            fine_bytes += ((size_t)frames[f].W * frames[f].rows * rgb_px + 255) & ~(size_t)255;
+        }
     }
     int rc;
+    if (resolve) {
+        if ((rc = grow(ctx, &ctx->d_fine, &ctx->fine_cap, fine_bytes)) != GBRT_OK) return rc;
+        size_t off = 0;
+        for (int f = 0; f < n; ++f) {
+            if (frames[f].aa <= 1) continue;
+            frames[f].out_rgb = (char*)ctx->d_fine + off;
+            frames[f].rgb_q0 = (int64_t)frames[f].row0 * frames[f].W;
+            off += ((size_t)frames[f].W * frames[f].rows * rgb_px + 255) & ~(size_t)255;
+        }
+    }
     if ((rc = grow(ctx, &ctx->d_hits, &ctx->hits_cap, (size_t)px * rec)) != GBRT_OK) return rc;
     if ((rc = grow(ctx, (void**)&ctx->d_vis, &ctx->vis_cap, (size_t)px * sizeof(unsigned))) != GBRT_OK) return rc;
     if ((rc = grow(ctx, (void**)&ctx->d_lmask, &ctx->lmask_cap, (size_t)px * sizeof(unsigned))) != GBRT_OK)
@@ -720,13 +777,14 @@ int render_frames(Ctx* ctx, FrameDev* frames, int n, bool use_graph) {
 
     const Grids gr = grids_for(ctx, precision);
     if (!use_graph) {
-        rc = enqueue_batch(ctx, ctx->stream, precision, bd, desc_bytes, gr);
+        rc = enqueue_batch(ctx, ctx->stream, precision, bd, desc_bytes, gr, resolve);
     } else {
         // replay a captured graph of {copy, memset, 4 kernels} when the batch
         // layout (buffers, counts, launch shape) is unchanged
         const long long key = ((long long)n << 40) ^ ((long long)precision << 36) ^ ((long long)gr.primary << 18) ^
                               (long long)gr.ao ^ ((long long)desc_bytes << 1);
-        if (!ctx->graph_valid || ctx->graph_key != key || memcmp(&ctx->graph_bd, &bd, sizeof(bd)) != 0) {
+        if (!ctx->graph_valid || ctx->graph_key != key || ctx->graph_resolve != resolve ||
+            memcmp(&ctx->graph_bd, &bd, sizeof(bd)) != 0) {
             if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
             ctx->graph_exec = nullptr;
             ctx->graph_valid = false;
@@ -737,7 +795,7 @@ int render_frames(Ctx* ctx, FrameDev* frames, int n, bool use_graph) {
             if (cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
                 return GBRT_EDEVICE;
             int64_t launches0 = ctx->launches;
-            int crc = enqueue_batch(ctx, ctx->capture_stream, precision, bd, desc_bytes, gr);
+            int crc = enqueue_batch(ctx, ctx->capture_stream, precision, bd, desc_bytes, gr, resolve);
             ctx->launches = launches0;
             cudaError_t ce = cudaStreamEndCapture(ctx->capture_stream, &graph);
             if (crc != GBRT_OK || ce != cudaSuccess) return crc != GBRT_OK ? crc : GBRT_EDEVICE;
@@ -746,10 +804,11 @@ int render_frames(Ctx* ctx, FrameDev* frames, int n, bool use_graph) {
             if (ce != cudaSuccess) return GBRT_EDEVICE;
             ctx->graph_valid = true;
             ctx->graph_key = key;
+            ctx->graph_resolve = resolve;
             ctx->graph_bd = bd;
         }
         rc = err_of(cudaGraphLaunch(ctx->graph_exec, ctx->stream));
-        ctx->launches += 4;
+        ctx->launches += resolve ? 5 : 4;
     }
     if (rc != GBRT_OK) return rc;
     cudaEventRecord(ctx->staging_done, ctx->stream);

@@ -29,7 +29,7 @@ static float float_of_ord(uint32_t o) {
 // when any object is invalid.
 __global__ void __launch_bounds__(256) k_scene_prep(const float* sph_in, int64_t S, const float* cyl_in, int64_t C,
                                                      const uint32_t* color, int32_t K, float4* obj, double2* obj64,
-                                                     float4* aabb, uint32_t* box) {
+                                                     float4* aabb, uint32_t* box, uint32_t* err) {
     const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const float big = 3.0e38f;
     float lo[3] = {big, big, big}, hi[3] = {-big, -big, -big};
@@ -85,6 +85,7 @@ __global__ void __launch_bounds__(256) k_scene_prep(const float* sph_in, int64_t
         aabb[2 * id + 1] = make_float4(hi[0], hi[1], hi[2], 0.0f);
         if (bad) {
             box[6] = 1u;
+            if (err) atomicOr(err, ERR_SCENE_DATA);
             for (int k = 0; k < 3; ++k) {
                 lo[k] = big;
                 hi[k] = -big;
@@ -167,10 +168,11 @@ __device__ __forceinline__ bool cell_reached(const float4* obj, int64_t id, cons
     return box_dist2(A.x + sm * B.x, A.y + sm * B.y, A.z + sm * B.z, lo, hi) <= lim * lim;
 }
 
-__global__ void __launch_bounds__(256) k_grid_count(const float4* aabb, const float4* obj, int64_t N, BuildP p,
-                                                     uint32_t* counts) {
+__global__ void __launch_bounds__(256) k_grid_count(const float4* aabb, const float4* obj, int64_t N,
+                                                     const BuildP* bp, uint32_t* counts) {
     int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= N) return;
+    const BuildP p = *bp;
     int c0[3], c1[3];
     cell_range(aabb, id, p, c0, c1);
     for (int z = c0[2]; z <= c1[2]; ++z)
@@ -180,10 +182,14 @@ __global__ void __launch_bounds__(256) k_grid_count(const float4* aabb, const fl
                     atomicAdd(counts + ((int64_t)z * p.n[1] + y) * p.n[0] + x, 1u);
 }
 
-__global__ void __launch_bounds__(256) k_grid_scatter(const float4* aabb, const float4* obj, int64_t N, BuildP p,
-                                                       const uint2* cells, uint32_t* cursor, uint32_t* items) {
+// Items past `items_cap` are dropped (a device-side rebuild that outgrew its
+// buffer; its finish step then disables the grid and flags the error).
+__global__ void __launch_bounds__(256) k_grid_scatter(const float4* aabb, const float4* obj, int64_t N,
+                                                       const BuildP* bp, const uint2* cells, uint32_t* cursor,
+                                                       uint32_t* items, uint64_t items_cap) {
     int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= N) return;
+    const BuildP p = *bp;
     int c0[3], c1[3];
     cell_range(aabb, id, p, c0, c1);
     for (int z = c0[2]; z <= c1[2]; ++z)
@@ -192,17 +198,19 @@ __global__ void __launch_bounds__(256) k_grid_scatter(const float4* aabb, const 
                 if (!cell_reached(obj, id, p, x, y, z)) continue;
                 int64_t c = ((int64_t)z * p.n[1] + y) * p.n[0] + x;
                 uint32_t slot = atomicAdd(cursor + c, 1u);
-                items[cells[c].x + slot] = (uint32_t)id;
+                const uint64_t at = (uint64_t)cells[c].x + slot;
+                if (at < items_cap) items[at] = (uint32_t)id;
             }
 }
 
 // Radius of the sphere about `ctr` that holds every object: sphere |c - ctr| + r,
 // cylinder max over both ends of |p - ctr| + r (FP64, rounded up to float).
-__global__ void __launch_bounds__(256) k_bound_radius(const double2* obj64, int64_t N, double cx, double cy,
-                                                       double cz, unsigned int* rbits) {
+__global__ void __launch_bounds__(256) k_bound_radius(const double2* obj64, int64_t N, const double* ctr,
+                                                       unsigned int* rbits) {
     int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     float rr = 0.0f;
     if (id < N) {
+        const double cx = ctr[0], cy = ctr[1], cz = ctr[2];
         const double2* q = obj64 + 4 * id;
         double2 q0 = q[0], q1 = q[1], q2 = q[2], q3 = q[3];
         double px = q0.x - cx, py = q0.y - cy, pz = q1.x - cz;
@@ -217,10 +225,12 @@ __global__ void __launch_bounds__(256) k_bound_radius(const double2* obj64, int6
 
 // Atomic scatter order is arbitrary: sort each cell's ids ascending (spheres
 // first, then cylinders; deterministic lists).
-__global__ void __launch_bounds__(256) k_cell_sort(const uint2* cells, int64_t ncells, uint32_t* items) {
+__global__ void __launch_bounds__(256) k_cell_sort(const uint2* cells, int64_t ncells, uint32_t* items,
+                                                    uint64_t items_cap) {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncells) return;
     uint2 cr = cells[c];
+    if ((uint64_t)cr.x + cr.y > items_cap) return;  // overflowed rebuild: the grid is disabled
     uint32_t* it = items + cr.x;
     for (uint32_t a = 1; a < cr.y; ++a) {
         uint32_t v = it[a];

@@ -22,6 +22,7 @@ DEVICE_PTRS, HOST_PTRS, BATCH_GRAPH = 0, 1, 2
 FP32, FP64 = 0, 1
 CAMERA_ORTHO, CAMERA_PINHOLE = 0, 1
 MAX_LIGHTS = 8
+MAX_AA = 4          # largest sub-pixel grid side (camera aa)
 MISS = 0xFFFFFFFF
 
 
@@ -32,7 +33,7 @@ class GbrtError(RuntimeError):
 
 
 class gbrt_camera(C.Structure):
-    _fields_ = [("kind", C.c_int32), ("reserved", C.c_int32), ("eye", C.c_double * 3), ("dir", C.c_double * 3),
+    _fields_ = [("kind", C.c_int32), ("aa", C.c_int32), ("eye", C.c_double * 3), ("dir", C.c_double * 3),
                 ("up", C.c_double * 3), ("right", C.c_double * 3), ("half_w", C.c_double), ("half_h", C.c_double)]
 
 
@@ -130,6 +131,7 @@ def ptr(x):
 def make_camera(cam) -> gbrt_camera:
     c = gbrt_camera()
     c.kind = int(cam.kind)
+    c.aa = int(getattr(cam, "aa", 1) or 1)
     for k in range(3):
         c.eye[k], c.dir[k], c.up[k], c.right[k] = cam.eye[k], cam.dir[k], cam.up[k], cam.right[k]
     c.half_w, c.half_h = float(cam.half_w), float(cam.half_h)
@@ -361,8 +363,10 @@ class Renderer:
         dev = f"cuda:{self.device}"
         dtype = t.float64 if params.precision == FP64 else t.float32
         rgb = t.empty((height, width, 3), dtype=dtype, device=dev)
-        hid = t.empty((height, width), dtype=t.int32, device=dev) if ids else None
-        av = t.empty((height, width), dtype=t.int32, device=dev) if vis else None
+        # hit ids and AO counts: one per sub-sample, in the m-times finer raster
+        m = max(1, int(getattr(camera, "aa", 1) or 1))
+        hid = t.empty((m * height, m * width), dtype=t.int32, device=dev) if ids else None
+        av = t.empty((m * height, m * width), dtype=t.int32, device=dev) if vis else None
         spp = params.ao_samples if ao_samples is None else ao_samples
         gbrt_render(self.ctx, scene, grid, camera, width, height, spp, lights, params, rgb, hid, av)
         return rgb, hid, av

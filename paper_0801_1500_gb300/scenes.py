@@ -348,6 +348,66 @@ def orbit_frames(scene: Scene, n_frames: int = 64, seed: int = 0):
     return out
 
 
+def bond_pairs(n_spheres: int, n_cylinders: int) -> np.ndarray:
+    """Sphere index pairs joined by the cylinders of a ``globule`` (consecutive
+    atoms of each chain, in cylinder order): int64 [C, 2]."""
+    pairs = []
+    start = 0
+    for length in chain_lengths(n_spheres, n_cylinders):
+        pairs += [(start + a - 1, start + a) for a in range(1, length)]
+        start += length
+    return np.asarray(pairs, np.int64).reshape(-1, 2)
+
+
+class MDTrajectory:
+    """Molecular-dynamics-like animation of a globule, frame by frame.
+
+    Frame k moves every atom of the base scene by a smooth bounded thermal
+    displacement -- amplitude/sqrt(3) times the sum over three seeded unit
+    vectors u_m of (sin(2 pi f_m k / period + phi_m) - sin(phi_m)), f_m = 1, 2,
+    3 -- and turns the whole molecule by ``spin_deg`` per frame about the +y
+    axis through the base box centre; bonds follow their atoms; radii and
+    colours stay. Frame 0 is the base scene.
+    """
+
+    def __init__(self, scene: Scene, amplitude: float = 0.3, period: int = 64, spin_deg: float = 2.0,
+                 seed: int = 0):
+        rng = np.random.Generator(np.random.PCG64(seed + 7919))
+        S = scene.n_spheres
+        self.base = scene
+        self.pairs = bond_pairs(S, scene.n_cylinders) if scene.n_cylinders else np.zeros((0, 2), np.int64)
+        self.c0 = scene.spheres[:, :3].astype(np.float64)
+        self.u = np.stack([_unit_vectors(rng, S) for _ in range(3)])          # [3, S, 3]
+        self.phi = rng.uniform(0.0, 2.0 * math.pi, (3, S))
+        self.amplitude, self.period, self.spin = float(amplitude), int(period), float(spin_deg)
+        lo, hi = scene.bounds()
+        self.centre = 0.5 * (lo + hi)
+
+    def spheres(self, k: int) -> np.ndarray:
+        disp = np.zeros_like(self.c0)
+        for m in range(3):
+            w = np.sin(2.0 * math.pi * (m + 1) * k / self.period + self.phi[m]) - np.sin(self.phi[m])
+            disp += w[:, None] * self.u[m]
+        c = self.c0 + (self.amplitude / math.sqrt(3.0)) * disp
+        th = math.radians(self.spin * k)
+        ct, st = math.cos(th), math.sin(th)
+        x, z = c[:, 0] - self.centre[0], c[:, 2] - self.centre[2]
+        c[:, 0] = self.centre[0] + ct * x + st * z
+        c[:, 2] = self.centre[2] - st * x + ct * z
+        out = self.base.spheres.copy()
+        out[:, :3] = c.astype(np.float32)
+        return out
+
+    def frame(self, k: int) -> Scene:
+        sp = self.spheres(k)
+        cy = self.base.cylinders.copy()
+        if len(self.pairs):
+            cy[:, 0:3] = sp[self.pairs[:, 0], :3]
+            cy[:, 3:6] = sp[self.pairs[:, 1], :3]
+        return Scene(spheres=sp, cylinders=cy, color_idx=self.base.color_idx, palette=self.base.palette,
+                     radius=self.base.radius, seed=self.base.seed)
+
+
 SERVE_RESOLUTIONS = [(256, 256), (965, 1137), (1920, 1080), (3860, 4548)]
 SERVE_SPP = [4, 16, 64]
 

@@ -71,3 +71,18 @@ def test_noalloc_rejects_frames_above_its_limit(G):
             G.gbrt_render_noalloc(scene, grid, S.ortho_camera(sc, W, H), W, H, 4, S.default_lights(),
                                   S.Params(), out)
         assert e.value.code == G.EINVAL
+
+
+def test_noalloc_rejects_supersampling(G):
+    import dataclasses
+
+    import torch
+    sc = S.make_scene([[0, 0, 0, 1.0]])
+    with G.Renderer(0) as r:
+        scene, grid = r.upload(sc)
+        W, H = 32, 32
+        out = torch.empty((H, W, 3), device="cuda")
+        cam = dataclasses.replace(S.ortho_camera(sc, W, H), aa=2)
+        with pytest.raises(G.GbrtError) as e:
+            G.gbrt_render_noalloc(scene, grid, cam, W, H, 4, S.default_lights(), S.Params(), out)
+        assert e.value.code == G.EINVAL
