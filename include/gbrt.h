@@ -50,6 +50,7 @@ extern "C" {
 #define GBRT_EDEVICE (-3)     /* CUDA runtime error / no device */
 #define GBRT_ETIMEDOUT (-4)   /* a bounded device wait ran out */
 #define GBRT_ETRAVERSAL (-5)  /* a grid walk exceeded its step bound */
+#define GBRT_ECAPACITY (-6)   /* a device-side grid rebuild outgrew its buffer */
 
 /* ---- flags ---- */
 #define GBRT_DEVICE_PTRS 0
@@ -237,11 +238,48 @@ GBRT_API int gbrt_scene_free(gbrt_ctx* ctx, gbrt_scene* scene);
  * (the reference count sizes the item array). */
 GBRT_API int gbrt_grid_build(gbrt_ctx* ctx, const gbrt_scene* scene, float lambda, gbrt_grid** out);
 
-/* Grid geometry (host only): cells per axis, padded box, total references. */
+/* Grid geometry: cells per axis, padded box, total references. Host only for
+ * a grid built by gbrt_grid_build; for a grid rebuilt on the device it first
+ * waits for the last rebuild's stream. */
 GBRT_API int gbrt_grid_info(const gbrt_grid* grid, int32_t dims[3], float lo[3], float hi[3], int64_t* refs,
                             int64_t* device_bytes);
 
 GBRT_API int gbrt_grid_free(gbrt_ctx* ctx, gbrt_grid* grid);
+
+/* Animated scenes (molecular-dynamics frames) -- an addition to the paper,
+ * which renders one static scene (its grid build is the "Preprocess" phase
+ * of Table 5). The two calls below replace that preprocess per frame without
+ * a host round trip, so the GPU can run a frame's rebuild right after the
+ * previous frame's render.
+ *
+ * gbrt_scene_update: new geometry for a resident scene -- sphere and
+ * cylinder arrays of the scene's own S and C, layouts as for
+ * gbrt_scene_upload; colours and palette stay. Asynchronous on the context's
+ * stream. Host arrays (flags GBRT_HOST_PTRS) are checked before any launch
+ * (GBRT_EINVAL) and copied through a staging buffer the scene allocates on
+ * its first update; page-locked host arrays are read asynchronously, so keep
+ * them unchanged until the stream has passed the copy. Device arrays are
+ * checked on the device: a bad value makes the next gbrt_sync return
+ * GBRT_EINVAL, and the scene's geometry is then unspecified until the next
+ * good update. Grids built on the scene keep their contents until
+ * gbrt_grid_rebuild. */
+GBRT_API int gbrt_scene_update(gbrt_ctx* ctx, gbrt_scene* scene, const float* spheres, const float* cylinders,
+                               int flags);
+
+/* gbrt_grid_rebuild: rebuild `grid` on the device for `scene`'s current
+ * geometry (the scene it was built for: same object count, else
+ * GBRT_EINVAL) with the grid's own cells-per-object density: scene box ->
+ * cells per axis -> count -> exclusive scan -> scatter -> per-cell sort ->
+ * bounding sphere, all on the context's stream; renders enqueued after it
+ * use the new grid. The first call allocates buffers with headroom (cells
+ * for 1.5x the target count, items for 1.5x the current references) and
+ * waits for the stream once; later calls neither allocate nor wait, except
+ * that a call which finds, from an earlier finished rebuild, that the items
+ * came within 1/8 of the buffer grows it (and waits). A rebuild whose
+ * references exceed the item buffer leaves the grid empty (renders then see
+ * no objects) and makes the next gbrt_sync return GBRT_ECAPACITY; the next
+ * rebuild after that sync grows the buffer. */
+GBRT_API int gbrt_grid_rebuild(gbrt_ctx* ctx, gbrt_grid* grid, const gbrt_scene* scene);
 
 /* Render one frame (Sec. 2's tachyon run: -res width height, AO with
  * ao_samples Monte-Carlo samples per pixel, lights, skylight).

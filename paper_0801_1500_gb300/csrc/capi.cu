@@ -118,6 +118,7 @@ FrameDev make_frame(const gbrt_scene* scene, const gbrt_grid* grid, const gbrt_c
         f.bg[k] = p->background[k];
         f.bg_f[k] = (float)p->background[k];
     }
+    f.grid_src = grid->dynamic ? grid->d_geom : nullptr;
     f.out_rgb = out_rgb;
     f.out_final = out_rgb;
     f.rgb_q0 = 0;
@@ -172,6 +173,7 @@ int read_error_word(Ctx* c) {
     }
     if (w & ERR_QUEUE_TIMEOUT) return GBRT_ETIMEDOUT;
     if (w & ERR_DDA_STEPS) return GBRT_ETRAVERSAL;
+    if (w & ERR_GRID_CAPACITY) return GBRT_ECAPACITY;
     if (w) return GBRT_EINVAL;
     return GBRT_OK;
 }
@@ -190,6 +192,7 @@ GBRT_API const char* gbrt_strerror(int code) {
         case GBRT_EDEVICE: return "CUDA device or runtime error";
         case GBRT_ETIMEDOUT: return "a bounded device wait ran out";
         case GBRT_ETRAVERSAL: return "a grid walk exceeded its step bound";
+        case GBRT_ECAPACITY: return "a device-side grid rebuild outgrew its buffer";
         default: return "unknown error";
     }
 }
@@ -335,6 +338,10 @@ GBRT_API int gbrt_grid_build(gbrt_ctx* ctx, const gbrt_scene* scene, float lambd
 GBRT_API int gbrt_grid_info(const gbrt_grid* grid, int32_t dims[3], float lo[3], float hi[3], int64_t* refs,
                             int64_t* device_bytes) {
     if (!grid) return GBRT_EINVAL;
+    if (grid->dynamic) {
+        int rc = grid_refresh_host(const_cast<gbrt_grid*>(grid));
+        if (rc != GBRT_OK) return rc;
+    }
     for (int k = 0; k < 3; ++k) {
         if (dims) dims[k] = grid->dev.n[k];
         if (lo) lo[k] = grid->dev.lo[k];
@@ -343,6 +350,25 @@ GBRT_API int gbrt_grid_info(const gbrt_grid* grid, int32_t dims[3], float lo[3],
     if (refs) *refs = grid->refs;
     if (device_bytes) *device_bytes = (int64_t)grid->bytes;
     return GBRT_OK;
+}
+
+GBRT_API int gbrt_scene_update(gbrt_ctx* ctx, gbrt_scene* scene, const float* spheres, const float* cylinders,
+                               int flags) {
+    if (!ctx || !scene) return GBRT_EINVAL;
+    if (flags & ~GBRT_HOST_PTRS) return GBRT_EINVAL;
+    if ((scene->S > 0 && !spheres) || (scene->C > 0 && !cylinders)) return GBRT_EINVAL;
+    if (scene->device != ctx->device) return GBRT_EINVAL;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return GBRT_EDEVICE;
+    return scene_update(ctx, scene, spheres, cylinders, flags);
+}
+
+GBRT_API int gbrt_grid_rebuild(gbrt_ctx* ctx, gbrt_grid* grid, const gbrt_scene* scene) {
+    if (!ctx || !grid || !scene) return GBRT_EINVAL;
+    if (scene->device != ctx->device) return GBRT_EINVAL;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return GBRT_EDEVICE;
+    return grid_rebuild(ctx, scene, grid);
 }
 
 GBRT_API int gbrt_grid_free(gbrt_ctx* ctx, gbrt_grid* grid) {
@@ -452,6 +478,11 @@ GBRT_API int gbrt_ao_probe(gbrt_ctx* ctx, const gbrt_scene* scene, const gbrt_gr
     memset(&cam, 0, sizeof(cam));
     gbrt_lights lights;
     memset(&lights, 0, sizeof(lights));
+    if (grid->dynamic) {
+        // the probe takes the geometry by value: wait for the device-side rebuild
+        int rc = grid_refresh_host(const_cast<gbrt_grid*>(grid));
+        if (rc != GBRT_OK) return rc;
+    }
     FrameDev f = make_frame(scene, grid, &cam, 1, 1, ao_samples, &lights, params, nullptr, nullptr, nullptr);
     return launch_ao_probe(ctx, f, pts, nrm, n, out_visibility);
 }

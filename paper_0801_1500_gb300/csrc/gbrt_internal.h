@@ -45,7 +45,7 @@ struct Ctx {
     cudaGraphExec_t graph_exec = nullptr;
     bool graph_valid = false;
     long long graph_key = 0;
-    bool graph_resolve = false;  // the captured graph ends with the supersampling resolve
+    int graph_extra = 0;  // optional passes in the captured graph (EXTRA_* bits)
     BatchDev graph_bd{};
     // per-kernel timing
     bool profiling = false;
@@ -64,6 +64,11 @@ struct Scene {
     float4* aabb = nullptr;  // [2 (S + C)]: lo (xyz), hi (xyz) per object
     float lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
     size_t bytes = 0;
+    // scene box on the device (order-preserving words: min xyz, max xyz,
+    // invalid flag); kept so device-side rebuilds read the current box
+    uint32_t* d_box = nullptr;
+    float* d_in = nullptr;  // staging of host geometry for gbrt_scene_update
+    bool box_stale = false;  // lo/hi above predate a device-side update
 
     SceneDev view() const {
         SceneDev v;
@@ -79,6 +84,28 @@ struct Scene {
     }
 };
 
+// Counts a device-side rebuild reports back (page-locked host copy).
+struct GridStat {
+    unsigned long long refs;
+    unsigned long long ncells;
+    unsigned int overflow;
+    unsigned int pad;
+};
+
+// Geometry handed to the build kernels through device memory, so a rebuild
+// can compute it on the device.
+struct BuildP {
+    float lo[3], inv_h[3], h[3];
+    int32_t n[3];
+    float pad;
+};
+struct BuildAux {
+    BuildP p;
+    double ctr[3];        // centre of the bounding sphere
+    unsigned int rbits;   // its radius (float bits, atomicMax)
+    unsigned int pad;
+};
+
 struct Grid {
     GridDev dev{};
     uint2* cells = nullptr;
@@ -86,6 +113,20 @@ struct Grid {
     int64_t refs = 0;
     size_t bytes = 0;
     float lambda = 0.f;
+    int64_t N = 0;  // objects of the scene it was built for
+    // device-side rebuilds (gbrt_grid_rebuild): the authoritative geometry is
+    // d_geom on the device; renders copy it into their frame descriptors
+    bool dynamic = false;
+    GridDev* d_geom = nullptr;
+    BuildAux* d_aux = nullptr;
+    uint32_t* d_counts = nullptr;
+    unsigned long long* d_sums = nullptr;
+    GridStat* d_stat = nullptr;
+    GridStat* h_stat = nullptr;
+    cudaEvent_t stat_ev = nullptr;
+    bool stat_pending = false;
+    int64_t cells_cap = 0, items_cap = 0;
+    cudaStream_t stream = nullptr;  // stream of the last rebuild
 };
 
 // scene_grid.cu: fill a caller-allocated object; on failure it frees what it
@@ -95,6 +136,14 @@ int scene_upload(Ctx* ctx, const float* spheres, int64_t S, const float* cyl, in
 void scene_release(Scene* s);
 int grid_build(Ctx* ctx, const Scene* s, float lambda, Grid* out);
 void grid_release(Grid* g);
+// device-side animation path: new geometry for a resident scene, and a grid
+// rebuild that neither allocates (after its first call) nor waits for the GPU
+int scene_update(Ctx* ctx, Scene* s, const float* spheres, const float* cyl, int flags);
+int grid_rebuild(Ctx* ctx, const Scene* s, Grid* g);
+// wait for a grid's last device-side rebuild and refresh the host copies
+int grid_refresh_host(Grid* g);
+// refresh a scene's host box after device-side updates (waits for `stream`)
+int scene_refresh_host(Scene* s, cudaStream_t stream);
 
 // capi.cu: argument checks and the frame descriptor of one render
 int check_frame_args(const gbrt_scene* scene, const gbrt_grid* grid, const gbrt_camera* cam, int32_t W, int32_t H,
@@ -110,7 +159,7 @@ int render_frames(Ctx* ctx, FrameDev* frames, int n, bool use_graph);
 // opt the AO kernels into their shared memory (once per device), then launch
 // the four wavefront kernels with grids sized for the current device.
 int configure_render_kernels();
-int enqueue_prepared(const BatchDev& bd, int precision, cudaStream_t stream, int block, int num_sms);
+int enqueue_prepared(const BatchDev& bd, int precision, cudaStream_t stream, int block, int num_sms, bool patch);
 int launch_ao_probe(Ctx* ctx, const FrameDev& f, const double* pts, const double* nrm, int64_t n, float* out);
 int launch_philox(Ctx* ctx, const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out);
 

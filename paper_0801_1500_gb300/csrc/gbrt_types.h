@@ -14,6 +14,7 @@ enum : uint32_t {
     ERR_DDA_STEPS = 1u,      // a grid walk exceeded nx + ny + nz + 3 steps
     ERR_SCENE_DATA = 2u,     // non-finite / non-positive scene values (device upload path)
     ERR_QUEUE_TIMEOUT = 4u,  // a bounded wait on the work queue ran out
+    ERR_GRID_CAPACITY = 8u,  // a device-side grid rebuild outgrew its item buffer
 };
 
 // Scene in the device layout: one record per object, indexed by global id
@@ -88,6 +89,9 @@ struct FrameDev {
     void* out_final;
     int64_t rgb_q0;
     int32_t aa;
+    // grid rebuilt on the device: its current geometry, copied over `grid`
+    // before the frame's kernels run (null for grids built on the host)
+    const GridDev* grid_src;
     // rows [row0, row0 + rows) of the image are rendered (a band, or all rows);
     // their tiling into primary-ray work items (tile_w x tile_h = 32)
     int32_t row0, rows;

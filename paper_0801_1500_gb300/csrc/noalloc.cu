@@ -120,7 +120,7 @@ extern "C" GBRT_API int gbrt_render_noalloc(const gbrt_scene* scene, const gbrt_
         bd.tile_h = th;
         bd.refill = refill;
         rc = cudaGetLastError() == cudaSuccess ? GBRT_OK : GBRT_EDEVICE;
-        if (rc == GBRT_OK) rc = enqueue_prepared(bd, params->precision, stream, block, sms);
+        if (rc == GBRT_OK) rc = enqueue_prepared(bd, params->precision, stream, block, sms, f.grid_src != nullptr);
     }
     if (prev != scene->device) cudaSetDevice(prev);
     return rc;

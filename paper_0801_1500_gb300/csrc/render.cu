@@ -534,6 +534,16 @@ __global__ void __launch_bounds__(256) k_shade(const __grid_constant__ BatchDev 
     }
 }
 
+// ---------------------------------------------------------------- grids rebuilt on the device
+
+// Frames whose grid was rebuilt on the device take its current geometry
+// before the frame's kernels run (their descriptors were written on the host).
+__global__ void k_patch_grids(const __grid_constant__ BatchDev b) {
+    FrameDev* frames = const_cast<FrameDev*>(b.frames);
+    for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < b.nframes; f += gridDim.x * blockDim.x)
+        if (frames[f].grid_src) frames[f].grid = *frames[f].grid_src;
+}
+
 // ---------------------------------------------------------------- supersampling
 
 // Box filter of supersampled frames: output pixel (i, j) is the mean of the
@@ -658,12 +668,20 @@ static Grids grids_for(Ctx* ctx, int precision) {
     return g;
 }
 
+// optional passes of a batch
+enum : int { EXTRA_RESOLVE = 1, EXTRA_PATCH = 2 };
+
 static int enqueue_batch(Ctx* ctx, cudaStream_t stream, int precision, const BatchDev& bd, size_t desc_bytes,
-                         const Grids& gr, bool resolve) {
+                         const Grids& gr, int extra) {
+    const bool resolve = (extra & EXTRA_RESOLVE) != 0;
     cudaError_t e = cudaMemcpyAsync(ctx->d_desc, ctx->h_desc, desc_bytes, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_counters, 0, ctx->counters_bytes_used, stream);
     if (e != cudaSuccess) return err_of(e);
     const int block = ctx->tuning.block;
+    if (extra & EXTRA_PATCH) {
+        k_patch_grids<<<1, 128, 0, stream>>>(bd);
+        ctx->launches++;
+    }
     // events between the kernels when timing (never inside a graph capture)
     const bool tm = ctx->profiling && stream == ctx->stream;
     auto mark = [&](int k) {
@@ -712,6 +730,7 @@ int render_frames(Ctx* ctx, FrameDev* frames, int n, bool use_graph) {
     long long tiles = 0;
     size_t fine_bytes = 0;  // finer-raster colours of the supersampled frames' bands
     bool resolve = false;
+    int extra = 0;
     const size_t rgb_px = 3 * (precision == GBRT_FP32 ? sizeof(float) : sizeof(double));
     for (int f = 0; f < n; ++f) {
         frames[f].tiles_x = (frames[f].W + tw - 1) / tw;
@@ -719,8 +738,10 @@ int render_frames(Ctx* ctx, FrameDev* frames, int n, bool use_graph) {
         frames[f].hit_base = px;
         px += (int64_t)frames[f].W * frames[f].rows;
         tiles += (long long)frames[f].tiles_x * frames[f].tiles_y;
+        if (frames[f].grid_src) extra |= EXTRA_PATCH;
         if (frames[f].aa > 1) {
             resolve = true;
+            extra |= EXTRA_RESOLVE;
             fine_bytes += ((size_t)frames[f].W * frames[f].rows * rgb_px + 255) & ~(size_t)255;
         }
     }
@@ -777,13 +798,13 @@ int render_frames(Ctx* ctx, FrameDev* frames, int n, bool use_graph) {
 
     const Grids gr = grids_for(ctx, precision);
     if (!use_graph) {
-        rc = enqueue_batch(ctx, ctx->stream, precision, bd, desc_bytes, gr, resolve);
+        rc = enqueue_batch(ctx, ctx->stream, precision, bd, desc_bytes, gr, extra);
     } else {
         // replay a captured graph of {copy, memset, 4 kernels} when the batch
         // layout (buffers, counts, launch shape) is unchanged
         const long long key = ((long long)n << 40) ^ ((long long)precision << 36) ^ ((long long)gr.primary << 18) ^
                               (long long)gr.ao ^ ((long long)desc_bytes << 1);
-        if (!ctx->graph_valid || ctx->graph_key != key || ctx->graph_resolve != resolve ||
+        if (!ctx->graph_valid || ctx->graph_key != key || ctx->graph_extra != extra ||
             memcmp(&ctx->graph_bd, &bd, sizeof(bd)) != 0) {
             if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
             ctx->graph_exec = nullptr;
@@ -795,7 +816,7 @@ int render_frames(Ctx* ctx, FrameDev* frames, int n, bool use_graph) {
             if (cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
                 return GBRT_EDEVICE;
             int64_t launches0 = ctx->launches;
-            int crc = enqueue_batch(ctx, ctx->capture_stream, precision, bd, desc_bytes, gr, resolve);
+            int crc = enqueue_batch(ctx, ctx->capture_stream, precision, bd, desc_bytes, gr, extra);
             ctx->launches = launches0;
             cudaError_t ce = cudaStreamEndCapture(ctx->capture_stream, &graph);
             if (crc != GBRT_OK || ce != cudaSuccess) return crc != GBRT_OK ? crc : GBRT_EDEVICE;
@@ -804,11 +825,11 @@ int render_frames(Ctx* ctx, FrameDev* frames, int n, bool use_graph) {
             if (ce != cudaSuccess) return GBRT_EDEVICE;
             ctx->graph_valid = true;
             ctx->graph_key = key;
-            ctx->graph_resolve = resolve;
+            ctx->graph_extra = extra;
             ctx->graph_bd = bd;
         }
         rc = err_of(cudaGraphLaunch(ctx->graph_exec, ctx->stream));
-        ctx->launches += resolve ? 5 : 4;
+        ctx->launches += 4 + (resolve ? 1 : 0) + ((extra & EXTRA_PATCH) ? 1 : 0);
     }
     if (rc != GBRT_OK) return rc;
     cudaEventRecord(ctx->staging_done, ctx->stream);
@@ -825,13 +846,14 @@ int configure_render_kernels() {
     return err_of(e);
 }
 
-int enqueue_prepared(const BatchDev& bd, int precision, cudaStream_t stream, int block, int num_sms) {
+int enqueue_prepared(const BatchDev& bd, int precision, cudaStream_t stream, int block, int num_sms, bool patch) {
     auto grid_of = [&](auto kernel, size_t smem) {
         int per_sm = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem) != cudaSuccess || per_sm < 1)
             per_sm = 1;
         return per_sm * num_sms;
     };
+    if (patch) k_patch_grids<<<1, 128, 0, stream>>>(bd);
     if (precision == GBRT_FP32) {
         const size_t smem = (block / 32) * sizeof(AoWarp<float>);
         k_primary<GBRT_FP32><<<grid_of(k_primary<GBRT_FP32>, 0), block, 0, stream>>>(bd);

@@ -106,12 +106,6 @@ __global__ void __launch_bounds__(256) k_scene_prep(const float* sph_in, int64_t
     }
 }
 
-// Grid geometry used by the build kernels (the same float values the walk uses).
-struct BuildP {
-    float lo[3], inv_h[3], h[3];
-    int32_t n[3];
-    float pad;
-};
 
 __device__ __forceinline__ int build_cell(const BuildP& p, int k, float x) {
     int c = (int)floorf((x - p.lo[k]) * p.inv_h[k]);
@@ -343,7 +337,7 @@ static bool host_scene_valid(const float* sph, int64_t S, const float* cyl, int6
         if (!(p[6] > 0)) return false;
         if (p[0] == p[3] && p[1] == p[4] && p[2] == p[5]) return false;
     }
-    for (int64_t i = 0; i < S + C; ++i)
+    for (int64_t i = 0; color && i < S + C; ++i)
         if (color[i] >= (uint32_t)K) return false;
     return true;
 }
@@ -354,6 +348,8 @@ void scene_release(Scene* s) {
     cudaFree(s->color);
     cudaFree(s->palette);
     cudaFree(s->aabb);
+    cudaFree(s->d_box);
+    cudaFree(s->d_in);
     *s = Scene();
 }
 
@@ -421,7 +417,7 @@ int scene_upload(Ctx* ctx, const float* spheres, int64_t S, const float* cyl, in
         if (N > 0) {
             int blocks = (int)((N + 255) / 256);
             k_scene_prep<<<blocks, 256, 0, ctx->stream>>>(d_sph_in, S, d_cyl_in, C, s->color, K, s->obj, s->obj64,
-                                                          s->aabb, d_box);
+                                                          s->aabb, d_box, nullptr);
             ctx->launches++;
             GB_TRY(cudaGetLastError());
         }
@@ -440,7 +436,7 @@ int scene_upload(Ctx* ctx, const float* spheres, int64_t S, const float* cyl, in
         cudaFree(d_sph_in);
         cudaFree(d_cyl_in);
     }
-    cudaFree(d_box);
+    s->d_box = d_box;  // kept: device-side rebuilds read the box from here
     return GBRT_OK;
 fail:
     cudaStreamSynchronize(ctx->stream);
@@ -456,7 +452,139 @@ fail:
 void grid_release(Grid* g) {
     cudaFree(g->cells);
     cudaFree(g->items);
+    cudaFree(g->d_geom);
+    cudaFree(g->d_aux);
+    cudaFree(g->d_counts);
+    cudaFree(g->d_sums);
+    cudaFree(g->d_stat);
+    cudaFreeHost(g->h_stat);
+    if (g->stat_ev) cudaEventDestroy(g->stat_ev);
     *g = Grid();
+}
+
+// a * b + c rounded twice, as on the host: the device must not fuse it, so a
+// device-side rebuild gets the same geometry as a host build
+__host__ __device__ inline double mul_add_rn(double a, double b, double c) {
+#ifdef __CUDA_ARCH__
+    return __dadd_rn(__dmul_rn(a, b), c);
+#else
+    return a * b + c;
+#endif
+}
+
+// Cells per axis for a box of extents E[3] and a target of `target` cells
+// (n_k = round(E_k (target / V)^(1/3)), clamped to [1, 1024]); host and device
+// evaluate the same expression.
+__host__ __device__ inline int64_t grid_dims(const double E[3], double kk, int32_t n[3]) {
+    int64_t nc = 1;
+    for (int k = 0; k < 3; ++k) {
+        double nk = floor(mul_add_rn(E[k], kk, 0.5));
+        nk = nk < 1.0 ? 1.0 : (nk > 1024.0 ? 1024.0 : nk);
+        n[k] = (int32_t)nk;
+        nc *= n[k];
+    }
+    return nc;
+}
+
+// Fill the grid geometry (GridDev fields, build parameters, bounding-sphere
+// centre) from the padded scene box; `cells_cap` > 0 caps the cell count.
+__host__ __device__ inline void grid_geometry(const float slo[3], const float shi[3], int64_t N, float lambda,
+                                              int64_t cells_cap, GridDev& d, BuildAux& a) {
+    float emax = fmaxf(shi[0] - slo[0], fmaxf(shi[1] - slo[1], shi[2] - slo[2]));
+    float pad = 1e-5f * fmaxf(emax, 1.0f);
+    double E[3], V = 1.0;
+    for (int k = 0; k < 3; ++k) {
+        d.lo[k] = slo[k] - pad;
+        d.hi[k] = shi[k] + pad;
+        E[k] = (double)d.hi[k] - (double)d.lo[k];
+        V *= E[k];
+    }
+    double target = fmin(fmax((double)lambda * (double)N, 1.0), 67108864.0);
+    double kk = cbrt(target / V);
+    d.ncells = grid_dims(E, kk, d.n);
+    for (int it = 0; cells_cap > 0 && d.ncells > cells_cap && it < 64; ++it) {
+        kk *= 0.98 * cbrt((double)cells_cap / (double)d.ncells);
+        d.ncells = grid_dims(E, kk, d.n);
+    }
+    if (cells_cap > 0 && d.ncells > cells_cap) {
+        d.n[0] = d.n[1] = d.n[2] = 1;
+        d.ncells = 1;
+    }
+    for (int k = 0; k < 3; ++k) {
+        const double nk = (double)d.n[k];
+        d.h64[k] = E[k] / nk;
+        d.inv_h64[k] = nk / E[k];
+        d.lo64[k] = (double)d.lo[k];
+        d.hi64[k] = (double)d.hi[k];
+        d.h[k] = (float)d.h64[k];
+        d.inv_h[k] = (float)d.inv_h64[k];
+        a.p.lo[k] = d.lo[k];
+        a.p.inv_h[k] = d.inv_h[k];
+        a.p.h[k] = d.h[k];
+        a.p.n[k] = d.n[k];
+        a.ctr[k] = 0.5 * ((double)d.lo[k] + d.hi[k]);
+    }
+    a.p.pad = pad;
+    a.rbits = 0u;
+    a.pad = 0u;
+    d.empty = N == 0 ? 1 : 0;
+}
+
+// Bounding sphere from its centre and the reduced radius bits.
+__host__ __device__ inline void grid_bound_sphere(const BuildAux& a, GridDev& d) {
+    float rb;
+    memcpy(&rb, &a.rbits, 4);
+    const double rpad = mul_add_rn((double)rb, 1.0 + 1e-5, (double)a.p.pad);
+    for (int k = 0; k < 3; ++k) {
+        d.bs64[k] = a.ctr[k];
+        d.bs[k] = (float)a.ctr[k];
+    }
+    d.bs64[3] = rpad;
+    // the float copy: pad for the rounding of the float centre too
+    d.bs[3] = (float)mul_add_rn(1e-6, fabs(a.ctr[0]) + fabs(a.ctr[1]) + fabs(a.ctr[2]) + 1.0, rpad);
+}
+
+__device__ __forceinline__ float float_of_ord_dev(uint32_t o) {
+    return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);
+}
+
+// Device-side rebuild, step 1 (one thread): geometry from the current scene box.
+__global__ void k_grid_geometry(const uint32_t* box, int64_t N, float lambda, int64_t cells_cap, const uint2* cells,
+                                const uint32_t* items, GridDev* geom, BuildAux* aux) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    float lo[3], hi[3];
+    for (int k = 0; k < 3; ++k) {
+        lo[k] = N > 0 ? float_of_ord_dev(box[k]) : 0.0f;
+        hi[k] = N > 0 ? float_of_ord_dev(box[3 + k]) : 0.0f;
+    }
+    GridDev d = *geom;
+    BuildAux a;
+    grid_geometry(lo, hi, N, lambda, cells_cap, d, a);
+    d.cells = cells;
+    d.items = items;
+    *geom = d;
+    *aux = a;
+}
+
+// Device-side rebuild, last step (one thread): bounding sphere, reference
+// count; a rebuild that outgrew its item buffer disables the grid (renders
+// then see no objects) and flags the context's error word.
+__global__ void k_grid_finish(GridDev* geom, const BuildAux* aux, const unsigned long long* total,
+                              unsigned long long items_cap, GridStat* stat, uint32_t* err) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    GridDev d = *geom;
+    grid_bound_sphere(*aux, d);
+    const unsigned long long refs = *total;
+    const unsigned int over = refs > items_cap ? 1u : 0u;
+    if (over) {
+        d.empty = 1;
+        atomicOr(err, ERR_GRID_CAPACITY);
+    }
+    *geom = d;
+    stat->refs = refs;
+    stat->ncells = (unsigned long long)d.ncells;
+    stat->overflow = over;
+    stat->pad = 0u;
 }
 
 int grid_build(Ctx* ctx, const Scene* s, float lambda, Grid* g) {
@@ -469,83 +597,39 @@ int grid_build(Ctx* ctx, const Scene* s, float lambda, Grid* g) {
     if (!(lambda > 0.0f)) lambda = 2.0f;
     g->lambda = lambda;
     const int64_t N = s->S + s->C;
+    g->N = N;
     GridDev& d = g->dev;
+    if (s->box_stale) {
+        rc = scene_refresh_host(const_cast<Scene*>(s), ctx->stream);
+        if (rc != GBRT_OK) return rc;
+    }
     {
-        float emax = std::max(s->hi[0] - s->lo[0], std::max(s->hi[1] - s->lo[1], s->hi[2] - s->lo[2]));
-        float pad = 1e-5f * std::max(emax, 1.0f);
-        double E[3], V = 1.0;
-        for (int k = 0; k < 3; ++k) {
-            d.lo[k] = s->lo[k] - pad;
-            d.hi[k] = s->hi[k] + pad;
-            E[k] = (double)d.hi[k] - (double)d.lo[k];
-            V *= E[k];
-        }
-        double target = std::min(std::max((double)lambda * (double)N, 1.0), 67108864.0);
-        double kk = cbrt(target / V);
-        d.ncells = 1;
-        for (int k = 0; k < 3; ++k) {
-            double nk = floor(E[k] * kk + 0.5);
-            nk = std::min(std::max(nk, 1.0), 1024.0);
-            d.n[k] = (int32_t)nk;
-            d.h64[k] = E[k] / nk;
-            d.inv_h64[k] = nk / E[k];
-            d.lo64[k] = (double)d.lo[k];
-            d.hi64[k] = (double)d.hi[k];
-            d.h[k] = (float)d.h64[k];
-            d.inv_h[k] = (float)d.inv_h64[k];
-            d.ncells *= d.n[k];
-        }
-        d.empty = N == 0 ? 1 : 0;
-        BuildP p;
-        for (int k = 0; k < 3; ++k) {
-            p.lo[k] = d.lo[k];
-            p.inv_h[k] = d.inv_h[k];
-            p.h[k] = d.h[k];
-            p.n[k] = d.n[k];
-        }
-        p.pad = pad;
+        BuildAux a;
+        grid_geometry(s->lo, s->hi, N, lambda, 0, d, a);
         const int64_t nc = d.ncells;
         GB_TRY(cudaMalloc(&g->cells, (size_t)nc * sizeof(uint2)));
         GB_TRY(cudaMalloc(&counts, (size_t)nc * sizeof(uint32_t)));
         GB_TRY(cudaMemsetAsync(counts, 0, (size_t)nc * sizeof(uint32_t), ctx->stream));
-        if (N > 0) {
-            k_grid_count<<<(int)((N + 255) / 256), 256, 0, ctx->stream>>>(s->aabb, s->obj, N, p, counts);
-            ctx->launches++;
-            GB_TRY(cudaGetLastError());
-        }
         const int64_t nb = (nc + SCAN_TILE - 1) / SCAN_TILE;
-        GB_TRY(cudaMalloc(&sums, (size_t)(nb + 2) * sizeof(unsigned long long)));
-        // bounding sphere about the box centre
-        const double ctr[3] = {0.5 * ((double)d.lo[0] + d.hi[0]), 0.5 * ((double)d.lo[1] + d.hi[1]),
-                               0.5 * ((double)d.lo[2] + d.hi[2])};
-        unsigned int* rbits = (unsigned int*)(sums + nb + 1);
-        GB_TRY(cudaMemsetAsync(rbits, 0, sizeof(unsigned long long), ctx->stream));
+        // sums: nb block sums, total, then the build parameters
+        GB_TRY(cudaMalloc(&sums, (size_t)(nb + 2) * sizeof(unsigned long long) + sizeof(BuildAux)));
+        BuildAux* d_aux = (BuildAux*)(sums + nb + 2);
+        GB_TRY(cudaMemcpyAsync(d_aux, &a, sizeof(a), cudaMemcpyHostToDevice, ctx->stream));
         if (N > 0) {
-            k_bound_radius<<<(int)((N + 255) / 256), 256, 0, ctx->stream>>>(s->obj64, N, ctr[0], ctr[1], ctr[2], rbits);
-            ctx->launches++;
+            k_grid_count<<<(int)((N + 255) / 256), 256, 0, ctx->stream>>>(s->aabb, s->obj, N, &d_aux->p, counts);
+            k_bound_radius<<<(int)((N + 255) / 256), 256, 0, ctx->stream>>>(s->obj64, N, d_aux->ctr, &d_aux->rbits);
+            ctx->launches += 2;
+            GB_TRY(cudaGetLastError());
         }
         k_scan_reduce<<<(int)nb, SCAN_T, 0, ctx->stream>>>(counts, nc, sums);
         k_scan_sums<<<1, SCAN_T, 0, ctx->stream>>>(sums, nb, sums + nb);
         k_scan_apply<<<(int)nb, SCAN_T, 0, ctx->stream>>>(counts, nc, sums, g->cells);
         ctx->launches += 3;
         GB_TRY(cudaGetLastError());
-        unsigned long long h_tail[2] = {0, 0};
-        GB_TRY(cudaMemcpyAsync(h_tail, sums + nb, sizeof(h_tail), cudaMemcpyDeviceToHost, ctx->stream));
+        GB_TRY(cudaMemcpyAsync(&h_total, sums + nb, sizeof(h_total), cudaMemcpyDeviceToHost, ctx->stream));
+        GB_TRY(cudaMemcpyAsync(&a.rbits, &d_aux->rbits, sizeof(a.rbits), cudaMemcpyDeviceToHost, ctx->stream));
         GB_TRY(cudaStreamSynchronize(ctx->stream));
-        h_total = h_tail[0];
-        {
-            float rb;
-            unsigned int bits = (unsigned int)(h_tail[1] & 0xFFFFFFFFull);
-            memcpy(&rb, &bits, 4);
-            double rpad = (double)rb * (1.0 + 1e-5) + (double)pad;
-            for (int k = 0; k < 3; ++k) {
-                d.bs64[k] = ctr[k];
-                d.bs[k] = (float)ctr[k];
-            }
-            d.bs64[3] = rpad;
-            // the float copy: pad for the rounding of the float centre too
-            d.bs[3] = (float)(rpad + 1e-6 * (fabs(ctr[0]) + fabs(ctr[1]) + fabs(ctr[2]) + 1.0));
-        }
+        grid_bound_sphere(a, d);
         if (h_total >= 0xFFFFFFFFull) {
             rc = GBRT_ENOMEM;
             goto fail;
@@ -555,9 +639,10 @@ int grid_build(Ctx* ctx, const Scene* s, float lambda, Grid* g) {
         if (N > 0) {
             cursor = counts;  // reuse as per-cell fill cursor
             GB_TRY(cudaMemsetAsync(cursor, 0, (size_t)nc * sizeof(uint32_t), ctx->stream));
-            k_grid_scatter<<<(int)((N + 255) / 256), 256, 0, ctx->stream>>>(s->aabb, s->obj, N, p, g->cells,
-                                                                            cursor, g->items);
-            k_cell_sort<<<(int)((nc + 255) / 256), 256, 0, ctx->stream>>>(g->cells, nc, g->items);
+            k_grid_scatter<<<(int)((N + 255) / 256), 256, 0, ctx->stream>>>(s->aabb, s->obj, N, &d_aux->p, g->cells,
+                                                                            cursor, g->items, (uint64_t)g->refs);
+            k_cell_sort<<<(int)((nc + 255) / 256), 256, 0, ctx->stream>>>(g->cells, nc, g->items,
+                                                                          (uint64_t)g->refs);
             ctx->launches += 2;
             GB_TRY(cudaGetLastError());
         }
@@ -575,6 +660,158 @@ fail:
     cudaFree(sums);
     grid_release(g);
     return rc;
+}
+
+// ---------------------------------------------------------------- animation path
+
+int scene_refresh_host(Scene* s, cudaStream_t stream) {
+    if (!s->box_stale) return GBRT_OK;
+    uint32_t h_box[8];
+    if (cudaStreamSynchronize(stream) != cudaSuccess ||
+        cudaMemcpy(h_box, s->d_box, sizeof(h_box), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return GBRT_EDEVICE;
+    const int64_t N = s->S + s->C;
+    for (int k = 0; k < 3; ++k) {
+        s->lo[k] = N > 0 ? float_of_ord(h_box[k]) : 0.0f;
+        s->hi[k] = N > 0 ? float_of_ord(h_box[3 + k]) : 0.0f;
+    }
+    s->box_stale = false;
+    return h_box[6] ? GBRT_EINVAL : GBRT_OK;
+}
+
+int scene_update(Ctx* ctx, Scene* s, const float* spheres, const float* cyl, int flags) {
+    const bool host = (flags & GBRT_HOST_PTRS) != 0;
+    const int64_t S = s->S, C = s->C, N = S + C;
+    if (N == 0) return GBRT_OK;
+    if (host && !host_scene_valid(spheres, S, cyl, C, nullptr, 0)) return GBRT_EINVAL;
+    const float* sph_in = spheres;
+    const float* cyl_in = cyl;
+    if (host) {
+        if (!s->d_in) {
+            if (cudaMalloc(&s->d_in, (size_t)(4 * S + 7 * C) * sizeof(float)) != cudaSuccess) {
+                s->d_in = nullptr;
+                return GBRT_ENOMEM;
+            }
+        }
+        float* dsph = s->d_in;
+        float* dcyl = s->d_in + 4 * S;
+        if (S > 0 && cudaMemcpyAsync(dsph, spheres, (size_t)S * 4 * sizeof(float), cudaMemcpyHostToDevice,
+                                     ctx->stream) != cudaSuccess)
+            return GBRT_EDEVICE;
+        if (C > 0 && cudaMemcpyAsync(dcyl, cyl, (size_t)C * 7 * sizeof(float), cudaMemcpyHostToDevice,
+                                     ctx->stream) != cudaSuccess)
+            return GBRT_EDEVICE;
+        sph_in = dsph;
+        cyl_in = dcyl;
+    }
+    // box words: min <- all ones (above every ordered float), max <- 0, flag <- 0
+    if (cudaMemsetAsync(s->d_box, 0xFF, 3 * sizeof(uint32_t), ctx->stream) != cudaSuccess ||
+        cudaMemsetAsync(s->d_box + 3, 0, 5 * sizeof(uint32_t), ctx->stream) != cudaSuccess)
+        return GBRT_EDEVICE;
+    k_scene_prep<<<(int)((N + 255) / 256), 256, 0, ctx->stream>>>(sph_in, S, cyl_in, C, s->color, s->K, s->obj,
+                                                                  s->obj64, s->aabb, s->d_box, ctx->d_err);
+    ctx->launches++;
+    s->box_stale = true;
+    return cudaGetLastError() == cudaSuccess ? GBRT_OK : GBRT_EDEVICE;
+}
+
+static int dyn_alloc(Grid* g, int64_t cells_cap, int64_t items_cap) {
+    // cells, counts, scan sums sized for cells_cap; items for items_cap
+    cudaFree(g->cells);
+    cudaFree(g->items);
+    cudaFree(g->d_counts);
+    cudaFree(g->d_sums);
+    g->cells = nullptr;
+    g->items = nullptr;
+    g->d_counts = nullptr;
+    g->d_sums = nullptr;
+    const int64_t nb = (cells_cap + SCAN_TILE - 1) / SCAN_TILE;
+    if (cudaMalloc(&g->cells, (size_t)cells_cap * sizeof(uint2)) != cudaSuccess ||
+        cudaMalloc(&g->items, (size_t)items_cap * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMalloc(&g->d_counts, (size_t)cells_cap * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMalloc(&g->d_sums, (size_t)(nb + 2) * sizeof(unsigned long long)) != cudaSuccess)
+        return GBRT_ENOMEM;
+    g->cells_cap = cells_cap;
+    g->items_cap = items_cap;
+    g->bytes = (size_t)cells_cap * (sizeof(uint2) + sizeof(uint32_t)) + (size_t)items_cap * sizeof(uint32_t);
+    g->dev.cells = g->cells;
+    g->dev.items = g->items;
+    return GBRT_OK;
+}
+
+int grid_rebuild(Ctx* ctx, const Scene* s, Grid* g) {
+    const int64_t N = s->S + s->C;
+    if (N != g->N) return GBRT_EINVAL;
+    int rc = GBRT_OK;
+    if (!g->dynamic) {
+        // first device-side rebuild: buffers with headroom for moving geometry
+        if (cudaMalloc(&g->d_geom, sizeof(GridDev)) != cudaSuccess ||
+            cudaMalloc(&g->d_aux, sizeof(BuildAux)) != cudaSuccess ||
+            cudaMalloc(&g->d_stat, sizeof(GridStat)) != cudaSuccess ||
+            cudaMallocHost(&g->h_stat, sizeof(GridStat)) != cudaSuccess ||
+            cudaEventCreateWithFlags(&g->stat_ev, cudaEventDisableTiming) != cudaSuccess)
+            return GBRT_ENOMEM;
+        cudaStreamSynchronize(ctx->stream);  // renders may still read the host-built arrays
+        const int64_t target = (int64_t)std::min(std::max((double)g->lambda * (double)N, 1.0), 67108864.0);
+        const int64_t cells_cap = std::max<int64_t>(g->dev.ncells, target + target / 2) + 4096;
+        const int64_t items_cap = std::max<int64_t>(g->refs + g->refs / 2, 4096);
+        if ((rc = dyn_alloc(g, cells_cap, items_cap)) != GBRT_OK) return rc;
+        if (cudaMemcpy(g->d_geom, &g->dev, sizeof(GridDev), cudaMemcpyHostToDevice) != cudaSuccess)
+            return GBRT_EDEVICE;
+        g->dynamic = true;
+    } else if (g->stat_pending && cudaEventQuery(g->stat_ev) == cudaSuccess) {
+        // the last finished rebuild's reference count: grow the item buffer
+        // ahead of need, or after an overflow
+        g->stat_pending = false;
+        const GridStat st = *g->h_stat;
+        g->refs = (int64_t)st.refs;
+        if (st.overflow || (int64_t)st.refs > g->items_cap - g->items_cap / 8) {
+            cudaStreamSynchronize(ctx->stream);
+            const int64_t items_cap = (int64_t)st.refs + (int64_t)st.refs / 2 + 4096;
+            if (items_cap >= (int64_t)0xFFFFFFFFll) return GBRT_ENOMEM;
+            if ((rc = dyn_alloc(g, g->cells_cap, items_cap)) != GBRT_OK) return rc;
+        }
+    }
+    g->stream = ctx->stream;
+    cudaStream_t st = ctx->stream;
+    const int64_t nc = g->cells_cap;
+    const int64_t nb = (nc + SCAN_TILE - 1) / SCAN_TILE;
+    const int blocksN = (int)((std::max<int64_t>(N, 1) + 255) / 256);
+    if (cudaMemsetAsync(g->d_counts, 0, (size_t)nc * sizeof(uint32_t), st) != cudaSuccess) return GBRT_EDEVICE;
+    k_grid_geometry<<<1, 32, 0, st>>>(s->d_box, N, g->lambda, nc, g->cells, g->items, g->d_geom, g->d_aux);
+    if (N > 0) {
+        k_grid_count<<<blocksN, 256, 0, st>>>(s->aabb, s->obj, N, &g->d_aux->p, g->d_counts);
+        k_bound_radius<<<blocksN, 256, 0, st>>>(s->obj64, N, g->d_aux->ctr, &g->d_aux->rbits);
+    }
+    k_scan_reduce<<<(int)nb, SCAN_T, 0, st>>>(g->d_counts, nc, g->d_sums);
+    k_scan_sums<<<1, SCAN_T, 0, st>>>(g->d_sums, nb, g->d_sums + nb);
+    k_scan_apply<<<(int)nb, SCAN_T, 0, st>>>(g->d_counts, nc, g->d_sums, g->cells);
+    if (N > 0) {
+        if (cudaMemsetAsync(g->d_counts, 0, (size_t)nc * sizeof(uint32_t), st) != cudaSuccess) return GBRT_EDEVICE;
+        k_grid_scatter<<<blocksN, 256, 0, st>>>(s->aabb, s->obj, N, &g->d_aux->p, g->cells, g->d_counts, g->items,
+                                                (uint64_t)g->items_cap);
+        k_cell_sort<<<(int)((nc + 255) / 256), 256, 0, st>>>(g->cells, nc, g->items, (uint64_t)g->items_cap);
+    }
+    k_grid_finish<<<1, 32, 0, st>>>(g->d_geom, g->d_aux, g->d_sums + nb, (unsigned long long)g->items_cap, g->d_stat,
+                                    ctx->d_err);
+    ctx->launches += N > 0 ? 9 : 5;
+    if (cudaGetLastError() != cudaSuccess) return GBRT_EDEVICE;
+    if (cudaMemcpyAsync(g->h_stat, g->d_stat, sizeof(GridStat), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaEventRecord(g->stat_ev, st) != cudaSuccess)
+        return GBRT_EDEVICE;
+    g->stat_pending = true;
+    return GBRT_OK;
+}
+
+int grid_refresh_host(Grid* g) {
+    if (!g->dynamic) return GBRT_OK;
+    if (g->stream && cudaStreamSynchronize(g->stream) != cudaSuccess) return GBRT_EDEVICE;
+    if (cudaMemcpy(&g->dev, g->d_geom, sizeof(GridDev), cudaMemcpyDeviceToHost) != cudaSuccess) return GBRT_EDEVICE;
+    if (g->stat_pending) {
+        g->stat_pending = false;
+        g->refs = (int64_t)g->h_stat->refs;
+    }
+    return GBRT_OK;
 }
 
 }  // namespace gbrt

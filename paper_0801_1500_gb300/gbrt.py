@@ -17,7 +17,7 @@ from . import build as _build
 
 LIB_PATH = _build.LIB
 
-OK, EINVAL, ENOMEM, EDEVICE, ETIMEDOUT, ETRAVERSAL = 0, -1, -2, -3, -4, -5
+OK, EINVAL, ENOMEM, EDEVICE, ETIMEDOUT, ETRAVERSAL, ECAPACITY = 0, -1, -2, -3, -4, -5, -6
 DEVICE_PTRS, HOST_PTRS, BATCH_GRAPH = 0, 1, 2
 FP32, FP64 = 0, 1
 CAMERA_ORTHO, CAMERA_PINHOLE = 0, 1
@@ -80,6 +80,8 @@ def _load():
         "gbrt_grid_build": ([P, P, f32, P], C.c_int),
         "gbrt_grid_info": ([P, P, P, P, P, P], C.c_int),
         "gbrt_grid_free": ([P, P], C.c_int),
+        "gbrt_scene_update": ([P, P, P, P, C.c_int], C.c_int),
+        "gbrt_grid_rebuild": ([P, P, P], C.c_int),
         "gbrt_render": ([P, P, P, C.POINTER(gbrt_camera), i32, i32, i32, C.POINTER(gbrt_lights),
                          C.POINTER(gbrt_params), P, P, P], C.c_int),
         "gbrt_render_batch": ([P, C.POINTER(gbrt_render_item), i32, C.c_int], C.c_int),
@@ -237,6 +239,24 @@ def gbrt_grid_info(grid):
 
 def gbrt_grid_free(ctx, grid):
     return _check(lib.gbrt_grid_free(ctx, grid), "gbrt_grid_free")
+
+
+def gbrt_scene_update(ctx, scene, spheres, cylinders, flags=None):
+    """New geometry for a resident scene (same counts): torch CUDA tensors or
+    numpy arrays (host; pinned ones are read asynchronously)."""
+    if flags is None:
+        flags = HOST_PTRS if isinstance(spheres, np.ndarray) else DEVICE_PTRS
+    if flags == HOST_PTRS:
+        if not (isinstance(spheres, np.ndarray) and spheres.dtype == np.float32 and spheres.flags.c_contiguous):
+            spheres = np.ascontiguousarray(spheres, np.float32)
+        if not (isinstance(cylinders, np.ndarray) and cylinders.dtype == np.float32
+                and cylinders.flags.c_contiguous):
+            cylinders = np.ascontiguousarray(cylinders, np.float32)
+    return _check(lib.gbrt_scene_update(ctx, scene, ptr(spheres), ptr(cylinders), int(flags)), "gbrt_scene_update")
+
+
+def gbrt_grid_rebuild(ctx, grid, scene):
+    return _check(lib.gbrt_grid_rebuild(ctx, grid, scene), "gbrt_grid_rebuild")
 
 
 def gbrt_render(ctx, scene, grid, camera, width, height, ao_samples, lights, params, out_rgb, out_hit_ids=None,

@@ -55,3 +55,32 @@ def test_traces():
     assert abs(gaps.mean() - 1 / 200) < 0.2 / 200
     scenes = S.serving_scenes(3, 1000, 20000)
     assert [s.n_objects for s in scenes][0] >= 900 and scenes[-1].n_objects <= 21000
+
+
+def test_md_trajectory_frames():
+    base = S.globule(300, 285, 10.0, seed=2)
+    traj = S.MDTrajectory(base, amplitude=0.3, period=16, spin_deg=3.0, seed=4)
+    f0 = traj.frame(0)
+    assert np.array_equal(f0.spheres, base.spheres) and np.array_equal(f0.cylinders, base.cylinders)
+    pairs = S.bond_pairs(300, 285)
+    assert pairs.shape == (285, 2)
+    for k in (1, 5, 11, 35):
+        f = traj.frame(k)
+        # bonds follow their atoms; radii and colours stay
+        assert np.array_equal(f.cylinders[:, 0:3], f.spheres[pairs[:, 0], :3])
+        assert np.array_equal(f.cylinders[:, 3:6], f.spheres[pairs[:, 1], :3])
+        assert np.array_equal(f.spheres[:, 3], base.spheres[:, 3])
+        assert np.array_equal(f.cylinders[:, 6], base.cylinders[:, 6])
+        # undo the spin: the thermal displacement is bounded by 2 sqrt(3) amplitude
+        th = np.radians(3.0 * k)
+        c = f.spheres[:, :3].astype(np.float64) - traj.centre
+        x = np.cos(th) * c[:, 0] - np.sin(th) * c[:, 2]
+        z = np.sin(th) * c[:, 0] + np.cos(th) * c[:, 2]
+        un = np.stack([x, c[:, 1], z], axis=1) + traj.centre
+        disp = np.linalg.norm(un - base.spheres[:, :3], axis=1)
+        assert disp.max() <= 2.0 * np.sqrt(3.0) * 0.3 + 1e-4
+        assert disp.max() > 0.05
+    # periodic in the thermal part: frame `period` differs from frame 0 by the spin only
+    assert np.array_equal(S.MDTrajectory(base, period=16, spin_deg=0.0, seed=4).frame(16).spheres.round(4),
+                          base.spheres.round(4))
+    assert np.array_equal(traj.frame(7).spheres, S.MDTrajectory(base, 0.3, 16, 3.0, 4).frame(7).spheres)
