@@ -312,7 +312,9 @@ constexpr int AO_MBOX = 8;
 template <class R>
 struct AoWarp {
     AoRay<R> ray[32];
-    unsigned delta[32];  // item index of pair p of ray r: p + delta[r]
+    unsigned delta[32];   // item index of pair p of ray r: p + delta[r] before split[r],
+    unsigned delta2[32];  // p + delta2[r] from split[r] on (the ray's second cell)
+    unsigned split[32];
     uint32_t self[32];
     uint32_t owner[32];  // ray whose pairs start at this position of the current chunk
     uint32_t mbox[32][AO_MBOX + 1];
@@ -425,7 +427,11 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
             }
         }
         if (exhausted && __ballot_sync(FULL, has) == 0) break;
-        // 2. every other active ray steps one cell
+        // 2. every active ray takes its next two cells (an any-hit query may
+        //    test objects past its first hit, so taking two at once is exact);
+        //    a fresh ray already holds its first
+        bool ending = false;
+        unsigned k2 = 0u, e2 = 0u;
         if (has && !fresh) {
             if (walk_next(w, overflow)) {
                 const uint2 cr = __ldg(cells + w.cell);
@@ -438,9 +444,19 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
                 has = false;
             }
         }
+        if (has) {
+            if (walk_next(w, overflow)) {
+                const uint2 cr = __ldg(cells + w.cell);
+                k2 = cr.x;
+                e2 = cr.x + cr.y;
+            } else {
+                ending = true;  // escapes unless this iteration's tests hit
+            }
+        }
         fresh = false;
         // 3. lay the warp's (ray, item) pairs out densely
-        const unsigned cnt = has ? e - k : 0u;
+        const unsigned n1 = has ? e - k : 0u;
+        const unsigned cnt = has ? n1 + (e2 - k2) : 0u;
         unsigned incl = cnt;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
@@ -452,6 +468,8 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
         if (T > 0) {
             const unsigned ex = incl - cnt;
             S.delta[lane] = k - ex;
+            S.delta2[lane] = k2 - (ex + n1);
+            S.split[lane] = ex + n1;
             // 4. map pairs to (ray, object), drop the own object and re-tests,
             //    queue the survivors; test whenever 32 are queued
             unsigned qn = 0;
@@ -465,7 +483,7 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
                 __syncwarp();
                 const unsigned p = base + lane < T ? base + lane : T - 1u;
                 const unsigned r = S.owner[31 - __clz(starts & (0xFFFFFFFFu >> (31 - lane)))];
-                const uint32_t id = __ldg(S.items[r] + (p + S.delta[r]));
+                const uint32_t id = __ldg(S.items[r] + (p + (p < S.split[r] ? S.delta[r] : S.delta2[r])));
                 uint32_t* slot = &S.mbox[r][id & (AO_MBOX - 1)];
                 const uint32_t seen = *slot;
                 const bool keep = base + lane < T && id != S.self[r] && seen != id;
@@ -491,8 +509,14 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
             }
             if (qn > 0) hitbits |= ao_test_batch(S, lane, qn);
         }
-        // 5. any hit occludes the ray
-        if (has && ((hitbits >> lane) & 1u)) has = false;
+        // 5. any hit occludes the ray; a ray whose walk ended escapes
+        if (has && ((hitbits >> lane) & 1u)) {
+            has = false;
+        } else if (has && ending) {
+            if (lbit) atomicOr(b.lmask + vslot, lbit);
+            else atomicAdd(b.vis + vslot, 1u);
+            has = false;
+        }
         __syncwarp();
     }
     if (overflow) atomicOr(b.err, ERR_DDA_STEPS);
