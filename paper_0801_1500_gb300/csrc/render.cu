@@ -308,13 +308,18 @@ struct __align__(16) AoRay {
 //                re-test of a missed object cannot hit, so skipping it is exact
 //   qr/qid       surviving (ray, object) pairs waiting for a full test batch
 constexpr int AO_MBOX = 8;
+// cells each active ray takes per lockstep iteration: further cells while it
+// holds fewer than AO_MIN_PAIRS candidates, at most AO_CELLS
+constexpr int AO_CELLS = 4;
+constexpr unsigned AO_MIN_PAIRS = 6;
 
 template <class R>
 struct AoWarp {
     AoRay<R> ray[32];
-    unsigned delta[32];   // item index of pair p of ray r: p + delta[r] before split[r],
-    unsigned delta2[32];  // p + delta2[r] from split[r] on (the ray's second cell)
-    unsigned split[32];
+    // item index of pair p of ray r: p + delta[g][r] for the last cell g whose
+    // pairs start at or before p (split[g][r])
+    unsigned delta[AO_CELLS][32];
+    unsigned split[AO_CELLS][32];
     uint32_t self[32];
     uint32_t owner[32];  // ray whose pairs start at this position of the current chunk
     uint32_t mbox[32][AO_MBOX + 1];
@@ -427,11 +432,10 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
             }
         }
         if (exhausted && __ballot_sync(FULL, has) == 0) break;
-        // 2. every active ray takes its next two cells (an any-hit query may
-        //    test objects past its first hit, so taking two at once is exact);
-        //    a fresh ray already holds its first
+        // 2. every active ray takes its next AO_CELLS cells (an any-hit query
+        //    may test objects past its first hit, so taking several at once is
+        //    exact); a fresh ray already holds its first
         bool ending = false;
-        unsigned k2 = 0u, e2 = 0u;
         if (has && !fresh) {
             if (walk_next(w, overflow)) {
                 const uint2 cr = __ldg(cells + w.cell);
@@ -444,19 +448,31 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
                 has = false;
             }
         }
-        if (has) {
-            if (walk_next(w, overflow)) {
-                const uint2 cr = __ldg(cells + w.cell);
-                k2 = cr.x;
-                e2 = cr.x + cr.y;
-            } else {
-                ending = true;  // escapes unless this iteration's tests hit
+        unsigned kg[AO_CELLS], ng[AO_CELLS];
+        kg[0] = k;
+        ng[0] = has ? e - k : 0u;
+#pragma unroll
+        for (int g = 1; g < AO_CELLS; ++g) {
+            kg[g] = 0u;
+            ng[g] = 0u;
+            unsigned sofar = 0u;
+#pragma unroll
+            for (int h = 0; h < g; ++h) sofar += ng[h];
+            if (has && !ending && sofar < AO_MIN_PAIRS) {
+                if (walk_next(w, overflow)) {
+                    const uint2 cr = __ldg(cells + w.cell);
+                    kg[g] = cr.x;
+                    ng[g] = cr.y;
+                } else {
+                    ending = true;  // escapes unless this iteration's tests hit
+                }
             }
         }
         fresh = false;
         // 3. lay the warp's (ray, item) pairs out densely
-        const unsigned n1 = has ? e - k : 0u;
-        const unsigned cnt = has ? n1 + (e2 - k2) : 0u;
+        unsigned cnt = 0u;
+#pragma unroll
+        for (int g = 0; g < AO_CELLS; ++g) cnt += ng[g];
         unsigned incl = cnt;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
@@ -467,9 +483,13 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
         unsigned hitbits = 0;
         if (T > 0) {
             const unsigned ex = incl - cnt;
-            S.delta[lane] = k - ex;
-            S.delta2[lane] = k2 - (ex + n1);
-            S.split[lane] = ex + n1;
+            unsigned run = ex;
+#pragma unroll
+            for (int g = 0; g < AO_CELLS; ++g) {
+                S.delta[g][lane] = kg[g] - run;
+                S.split[g][lane] = run;
+                run += ng[g];
+            }
             // 4. map pairs to (ray, object), drop the own object and re-tests,
             //    queue the survivors; test whenever 32 are queued
             unsigned qn = 0;
@@ -483,7 +503,11 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
                 __syncwarp();
                 const unsigned p = base + lane < T ? base + lane : T - 1u;
                 const unsigned r = S.owner[31 - __clz(starts & (0xFFFFFFFFu >> (31 - lane)))];
-                const uint32_t id = __ldg(S.items[r] + (p + (p < S.split[r] ? S.delta[r] : S.delta2[r])));
+                unsigned di = S.delta[0][r];
+#pragma unroll
+                for (int g = 1; g < AO_CELLS; ++g)
+                    if (p >= S.split[g][r]) di = S.delta[g][r];
+                const uint32_t id = __ldg(S.items[r] + (p + di));
                 uint32_t* slot = &S.mbox[r][id & (AO_MBOX - 1)];
                 const uint32_t seen = *slot;
                 const bool keep = base + lane < T && id != S.self[r] && seen != id;
