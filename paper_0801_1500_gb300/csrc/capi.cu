@@ -90,6 +90,9 @@ FrameDev make_frame(const gbrt_scene* scene, const gbrt_grid* grid, const gbrt_c
     f.spp = spp;
     f.shadows = p->shadows ? 1 : 0;
     f.jobs_per_hit = spp + (f.shadows ? lights->n : 0);
+    f.jph_magic = f.jobs_per_hit > 1
+                      ? (uint32_t)(((1ull << 32) + (uint64_t)f.jobs_per_hit - 1) / (uint64_t)f.jobs_per_hit)
+                      : 0u;
     f.frame = p->frame;
     f.seed_lo = (uint32_t)(p->seed & 0xFFFFFFFFull);
     f.seed_hi = (uint32_t)(p->seed >> 32);

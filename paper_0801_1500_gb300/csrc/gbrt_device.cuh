@@ -157,7 +157,7 @@ struct GridP;
 template <>
 struct GridP<float> {
     static __device__ __forceinline__ float bs(const GridDev& g, int k) { return g.bs[k]; }
-    static __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+    static __device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
     static __device__ __forceinline__ float lo(const GridDev& g, int k) { return g.lo[k]; }
     static __device__ __forceinline__ float hi(const GridDev& g, int k) { return g.hi[k]; }
     static __device__ __forceinline__ float h(const GridDev& g, int k) { return g.h[k]; }

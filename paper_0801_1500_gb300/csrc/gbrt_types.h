@@ -63,6 +63,7 @@ struct FrameDev {
     int32_t W, H, spp;
     int32_t shadows;       // 1: one shadow ray per light the surface faces
     int32_t jobs_per_hit;  // AO samples + shadow rays of one hit
+    uint32_t jph_magic;    // ceil(2^32 / jobs_per_hit) when jobs_per_hit > 1 (division by multiply)
     uint32_t frame;
     uint32_t seed_lo, seed_hi;
     int32_t precision;

@@ -377,7 +377,17 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
                     const FrameDev& F = b.frames[f];
                     const unsigned long long jl = jj - b.job_off[f];
                     const uint32_t jph = (uint32_t)F.jobs_per_hit;
-                    const uint32_t h = jl < 0xFFFFFFFFull ? (uint32_t)jl / jph : (uint32_t)(jl / jph);
+                    uint32_t h;
+                    if (jl >= 0xFFFFFFFFull) {
+                        h = (uint32_t)(jl / jph);
+                    } else if (jph > 1u) {
+                        // jl / jph by the multiplier ceil(2^32 / jph): the product's
+                        // high word is the quotient or one more
+                        h = __umulhi((uint32_t)jl, F.jph_magic);
+                        if ((unsigned long long)h * jph > jl) --h;
+                    } else {
+                        h = (uint32_t)jl;
+                    }
                     const uint32_t smp = (uint32_t)(jl - (unsigned long long)h * jph);
                     vslot = F.hit_base + h;
                     V3<R> o, n;
