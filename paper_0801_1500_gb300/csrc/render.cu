@@ -63,28 +63,30 @@ __device__ __forceinline__ V3<float> view_dir_f(const FrameDev& f, uint32_t q) {
 }
 
 // FP64 root of object `id`'s quadratic along o + t d by Newton's method from
-// an FP32 root t: F(t) = |w_p(t)|^2 - r^2 with w(t) = o + t d - p0 and w_p its
-// part perpendicular to the axis a (all of w for a sphere, a = 0);
-// F'(t) = 2 d_p . w_p. F and F' are evaluated in FP64; the small correction
-// F/F' is divided in FP32 (its relative error stays far below FP64 rounding of
-// t). Two steps carry an FP32-accurate root to FP64 accuracy on non-grazing
-// rays. False when the steps do not settle (a grazing ray): the caller keeps
-// the FP32 root.
+// an FP32 root t: F(t) = |f_p + t d_p|^2 - r^2 = A t^2 + 2 B t + C, with f_p
+// and d_p the parts of o - p0 and d perpendicular to the axis a (all of them
+// for a sphere, a = 0): A = d_p.d_p, B = f_p.d_p, C = f_p.f_p - r^2, and
+// F'(t) = 2 (A t + B). The coefficients are formed once in FP64 (their
+// cancellation near the root costs about |f_p|^2 / r of FP64's precision,
+// orders below the FP32 root's error); the small correction F/F' is divided
+// in FP32. Two steps carry an FP32-accurate root to FP64 accuracy on
+// non-grazing rays. False when the steps do not settle (a grazing ray): the
+// caller keeps the FP32 root.
 __device__ __forceinline__ bool newton_root64(const double2* obj64, uint32_t id, V3<double> o, V3<double> d,
                                               double& t) {
     V3<double> p0, a;
     double L, r;
     Obj<double>::load(obj64, id, p0, a, L, r);
     const V3<double> f0 = o - p0;
-    const double da = dot(d, a);
-    const V3<double> dp = madd(d, -da, a);
+    const V3<double> fp = madd(f0, -dot(f0, a), a);
+    const V3<double> dp = madd(d, -dot(d, a), a);
+    const double A = dot(dp, dp), B = dot(fp, dp), C = fma(-r, r, dot(fp, fp));
+    const double A2 = 2.0 * A, B2 = 2.0 * B;
     double tt = t, corr = 0.0;
 #pragma unroll
     for (int it = 0; it < 2; ++it) {
-        const V3<double> w = madd(f0, tt, d);
-        const V3<double> wp = madd(w, -dot(w, a), a);
-        const double F = dot(wp, wp) - r * r;
-        const double Fp = 2.0 * dot(dp, wp);
+        const double F = fma(fma(A, tt, B2), tt, C);
+        const double Fp = fma(A2, tt, B2);
         corr = (double)__fdividef((float)F, (float)Fp);
         tt -= corr;
     }
