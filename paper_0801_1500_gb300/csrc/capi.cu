@@ -115,6 +115,7 @@ FrameDev make_frame(const gbrt_scene* scene, const gbrt_grid* grid, const gbrt_c
     f.k_s_f = (float)f.k_s;
     f.phong_f = (float)f.phong;
     f.eps = p->eps;
+    f.eps_f = (float)p->eps;
     f.ao_maxdist = p->ao_maxdist;
     f.ao_maxdist_f = (float)p->ao_maxdist;
     for (int k = 0; k < 3; ++k) {

@@ -76,6 +76,7 @@ struct FrameDev {
     double sky_kao, k_d, k_s, phong;
     float sky_kao_f, k_d_f, k_s_f, phong_f;
     double eps, ao_maxdist;
+    float eps_f;
     float ao_maxdist_f;
     double bg[3];
     float bg_f[3];

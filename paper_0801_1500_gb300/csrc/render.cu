@@ -68,10 +68,12 @@ __device__ __forceinline__ V3<float> view_dir_f(const FrameDev& f, uint32_t q) {
 // for a sphere, a = 0): A = d_p.d_p, B = f_p.d_p, C = f_p.f_p - r^2, and
 // F'(t) = 2 (A t + B). The coefficients are formed once in FP64 (their
 // cancellation near the root costs about |f_p|^2 / r of FP64's precision,
-// orders below the FP32 root's error); the small correction F/F' is divided
-// in FP32. Two steps carry an FP32-accurate root to FP64 accuracy on
-// non-grazing rays. False when the steps do not settle (a grazing ray): the
-// caller keeps the FP32 root.
+// orders below the FP32 root's error). The steps divide by F' at the FP32
+// root, rounded to FP32 (a chord step: F' changes by a relative ~1e-7 over
+// the correction, so each step still gains ~7 digits) -- one FP32 reciprocal
+// and no further conversions. Two steps carry an FP32-accurate root to FP64
+// accuracy on non-grazing rays. False when the steps do not settle (a
+// grazing ray): the caller keeps the FP32 root.
 __device__ __forceinline__ bool newton_root64(const double2* obj64, uint32_t id, V3<double> o, V3<double> d,
                                               double& t) {
     V3<double> p0, a;
@@ -81,13 +83,12 @@ __device__ __forceinline__ bool newton_root64(const double2* obj64, uint32_t id,
     const V3<double> fp = madd(f0, -dot(f0, a), a);
     const V3<double> dp = madd(d, -dot(d, a), a);
     const double A = dot(dp, dp), B = dot(fp, dp), C = fma(-r, r, dot(fp, fp));
-    const double A2 = 2.0 * A, B2 = 2.0 * B;
+    const double B2 = 2.0 * B;
+    const double rFp = (double)__fdividef(1.0f, (float)fma(2.0 * A, t, B2));
     double tt = t, corr = 0.0;
 #pragma unroll
     for (int it = 0; it < 2; ++it) {
-        const double F = fma(fma(A, tt, B2), tt, C);
-        const double Fp = fma(A2, tt, B2);
-        corr = (double)__fdividef((float)F, (float)Fp);
+        corr = fma(fma(A, tt, B2), tt, C) * rFp;
         tt -= corr;
     }
     const bool ok = fabs(corr) <= 1e-6 * (fabs(tt) + 1.0) && isfinite(tt);
@@ -108,12 +109,12 @@ __device__ __forceinline__ bool nearest_fp32_refined(const FrameDev& f, V3<doubl
     V3<float> oe = to_f(madd(o64, (double)te0, d64));
     Nearest<float> h;
     if (!trace_nearest<float>(f.grid, f.scene, oe, df, 0.0f, inf, h, overflow)) return false;
-    double ta = (double)te0 + (double)h.t1;
+    double ta = (double)(te0 + h.t1);
     newton_root64(f.scene.obj64, h.id1, o64, d64, ta);
     id = h.id1;
     t64 = ta;
     if (h.id2 != GBRT_MISS && (h.t2 - h.t1) <= 1e-4f * (h.t1 + te0)) {
-        double tb = (double)te0 + (double)h.t2;
+        double tb = (double)(te0 + h.t2);
         newton_root64(f.scene.obj64, h.id2, o64, d64, tb);
         if (tb < ta || (tb == ta && h.id2 < h.id1)) {
             id = h.id2;
@@ -231,20 +232,21 @@ __global__ void __launch_bounds__(256) k_primary(const __grid_constant__ BatchDe
             const int64_t slot = F.hit_base + base + __popc(hm & ((1u << lane) - 1u));
             if (MODE == GBRT_FP32) {
                 // FP64 hit point and its foot q on the generator (centre or
-                // axis); the outward unit normal in FP32; the AO origin one eps
-                // along the normal facing the ray from the re-projected
-                // surface point q + r n_out
+                // axis); w_p = p - q has length r (to FP64 accuracy at the
+                // refined root), so the re-projected surface point plus eps
+                // along the normal facing the ray is q + (1 +- eps/r) w_p; the
+                // unit normal itself is needed in FP32 only
                 V3<double> p0, a;
                 double L, r;
                 Obj<double>::load(F.scene.obj64, id, p0, a, L, r);
                 const V3<double> w = madd(o64 - p0, t64, d64);
                 const double wa = dot(w, a);
-                const V3<double> qq = madd(p0, wa, a);
-                V3<float> nf = to_f(madd(w, -wa, a));
+                const V3<double> wp = madd(w, -wa, a);
+                V3<float> nf = to_f(wp);
                 nf = rsqrtf(dot(nf, nf)) * nf;
                 const bool flip = dot(view_dir_f(F, q), nf) > 0.0f;
-                // surface point + eps n_face = q + r n_out + eps n_face
-                const V3<double> ao_o = madd(qq, flip ? r - F.eps : r + F.eps, to_d(nf));
+                const double er = (double)__fdividef(F.eps_f, (float)r);
+                const V3<double> ao_o = madd(madd(p0, wa, a), flip ? 1.0 - er : 1.0 + er, wp);
                 if (flip) nf = v3(-nf.x, -nf.y, -nf.z);
                 HitIO<float>::store_f(b.hits, slot, ao_o, nf, q | (flip ? HIT_INSIDE : 0u), id);
             } else {
