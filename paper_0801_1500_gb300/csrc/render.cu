@@ -331,6 +331,7 @@ struct AoWarp {
     const uint32_t* items[32];
     uint32_t qid[64];
     uint32_t qr[64];
+    uint2 fifo[32][AO_CELLS];  // cells a ray has loaded but not yet taken, oldest first
 };
 
 // Test queued pairs [0, n) (1 <= n <= 32), one per lane (lanes past n redo
@@ -361,7 +362,8 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
     const int refill = b.refill;
     bool has = false, fresh = false, exhausted = false, overflow = false;
     Walk<R> w;
-    uint32_t k = 0, e = 0;
+    unsigned nf = 0;      // cells waiting in this lane's fifo
+    bool wend = false;    // the walk has no further cells
     uint32_t lbit = 0;  // 0: an AO sample; 1 << l: the shadow ray toward light l
     int64_t vslot = 0;
     const uint2* cells = nullptr;
@@ -432,11 +434,10 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
                         S.self[lane] = self;
 #pragma unroll
                         for (int m = 0; m < AO_MBOX; ++m) S.mbox[lane][m] = GBRT_MISS;
-                        const uint2 cr = __ldg(cells + w.cell);
-                        k = cr.x;
-                        e = cr.x + cr.y;
+                        nf = 0;
+                        wend = false;
                         has = true;
-                        fresh = true;
+                        fresh = true;  // the walk stands on its first cell, not yet loaded
                     } else if (lbit) {
                         atomicOr(b.lmask + vslot, lbit);  // misses the objects' bounds: escapes
                     } else {
@@ -446,43 +447,63 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
             }
         }
         if (exhausted && __ballot_sync(FULL, has) == 0) break;
-        // 2. every active ray takes its next AO_CELLS cells (an any-hit query
-        //    may test objects past its first hit, so taking several at once is
-        //    exact); a fresh ray already holds its first
+        // 2. every active ray takes its next cells: its first, and further ones
+        //    while it holds fewer than AO_MIN_PAIRS candidates (an any-hit
+        //    query may test objects past its first hit, so taking several at
+        //    once is exact). The ray's fifo is first topped up to AO_CELLS
+        //    loaded cells -- the new cells' loads are independent and overlap
+        //    -- and the cells it does not take wait there for the next iteration
         bool ending = false;
-        if (has && !fresh) {
-            if (walk_next(w, overflow)) {
-                const uint2 cr = __ldg(cells + w.cell);
-                k = cr.x;
-                e = cr.x + cr.y;
-            } else {
-                // walked out: escapes
-                if (lbit) atomicOr(b.lmask + vslot, lbit);
-                else atomicAdd(b.vis + vslot, 1u);
-                has = false;
-            }
-        }
         unsigned kg[AO_CELLS], ng[AO_CELLS];
-        kg[0] = k;
-        ng[0] = has ? e - k : 0u;
+        unsigned avail = 0u;
 #pragma unroll
-        for (int g = 1; g < AO_CELLS; ++g) {
-            kg[g] = 0u;
-            ng[g] = 0u;
-            unsigned sofar = 0u;
-#pragma unroll
-            for (int h = 0; h < g; ++h) sofar += ng[h];
-            if (has && !ending && sofar < AO_MIN_PAIRS) {
-                if (walk_next(w, overflow)) {
-                    const uint2 cr = __ldg(cells + w.cell);
-                    kg[g] = cr.x;
-                    ng[g] = cr.y;
-                } else {
-                    ending = true;  // escapes unless this iteration's tests hit
+        for (int g = 0; g < AO_CELLS; ++g) {
+            uint2 cr = make_uint2(0u, 0u);
+            if (has) {
+                if ((unsigned)g < nf) {
+                    cr = S.fifo[lane][g];
+                    ++avail;
+                } else if (!wend) {
+                    bool next = fresh;
+                    fresh = false;
+                    if (!next) next = walk_next(w, overflow);
+                    if (next) {
+                        cr = __ldg(cells + w.cell);
+                        ++avail;
+                    } else {
+                        wend = true;
+                    }
                 }
             }
+            kg[g] = cr.x;
+            ng[g] = cr.y;
         }
-        fresh = false;
+        if (has && avail == 0u) {
+            // walked out: escapes
+            if (lbit) atomicOr(b.lmask + vslot, lbit);
+            else atomicAdd(b.vis + vslot, 1u);
+            has = false;
+        }
+        if (has) {
+            // take cells 0..m-1; the rest go back to the fifo
+            unsigned m = 1u, sofar = ng[0];
+#pragma unroll
+            for (int g = 1; g < AO_CELLS; ++g) {
+                if ((unsigned)g < avail && sofar < AO_MIN_PAIRS && m == (unsigned)g) {
+                    sofar += ng[g];
+                    m = (unsigned)g + 1u;
+                }
+            }
+#pragma unroll
+            for (int g = 1; g < AO_CELLS; ++g) {
+                if ((unsigned)g >= m) {
+                    if ((unsigned)g < avail) S.fifo[lane][g - m] = make_uint2(kg[g], ng[g]);
+                    ng[g] = 0u;
+                }
+            }
+            nf = avail - m;
+            ending = wend && nf == 0u;  // escapes unless this iteration's tests hit
+        }
         // 3. lay the warp's (ray, item) pairs out densely
         unsigned cnt = 0u;
 #pragma unroll
