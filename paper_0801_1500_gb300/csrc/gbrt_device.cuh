@@ -221,33 +221,37 @@ __device__ __forceinline__ bool clip_grid(const GridDev& g, V3<R> o, V3<R> d, R 
     return clip_grid(g, o, d, inv_dir(d), tmin, tmax, t0, t1);
 }
 
-// Amanatides & Woo (1987) traversal state: current cell, per-axis step, the t
-// of the next boundary crossing on each axis and the t between crossings.
+// Amanatides & Woo (1987) traversal state: the current cell's index, per
+// axis the steps left before the grid ends, the index change of one step, the
+// t of the next boundary crossing and the t between crossings.
 template <class R>
 struct Walk {
-    int cx, cy, cz;
-    int sx, sy, sz;
+    int rx, ry, rz;
+    int stx, sty, stz;
     R tnx, tny, tnz;
     R tdx, tdy, tdz;
     R t1;
     int cell;
     int left;
-    int nx, ny, nz;
 };
 
 template <class R>
-__device__ __forceinline__ void axis_setup(const GridDev& g, int k, R o, R d, R inv, int c, int& s, R& tn, R& td) {
+__device__ __forceinline__ void axis_setup(const GridDev& g, int k, R o, R d, R inv, int c, int stride, int& r,
+                                           int& st, R& tn, R& td) {
     R inf = Num<R>::inf();
     if (d > R(0)) {
-        s = 1;
+        r = g.n[k] - 1 - c;
+        st = stride;
         tn = (GridP<R>::lo(g, k) + R(c + 1) * GridP<R>::h(g, k) - o) * inv;
         td = GridP<R>::h(g, k) * inv;
     } else if (d < R(0)) {
-        s = -1;
+        r = c;
+        st = -stride;
         tn = (GridP<R>::lo(g, k) + R(c) * GridP<R>::h(g, k) - o) * inv;
         td = -GridP<R>::h(g, k) * inv;
     } else {
-        s = 0;
+        r = 0;
+        st = 0;
         tn = inf;
         td = inf;
     }
@@ -267,18 +271,14 @@ __device__ __forceinline__ bool walk_start(const GridDev& g, V3<R> o, V3<R> d, R
     const V3<R> inv = inv_dir(d);
     if (g.empty || !clip_grid(g, o, d, inv, tmin, tmax, t0, t1)) return false;
     V3<R> p = madd(o, t0, d);
-    w.cx = cell_of(g, 0, p.x);
-    w.cy = cell_of(g, 1, p.y);
-    w.cz = cell_of(g, 2, p.z);
-    axis_setup(g, 0, o.x, d.x, inv.x, w.cx, w.sx, w.tnx, w.tdx);
-    axis_setup(g, 1, o.y, d.y, inv.y, w.cy, w.sy, w.tny, w.tdy);
-    axis_setup(g, 2, o.z, d.z, inv.z, w.cz, w.sz, w.tnz, w.tdz);
+    const int cx = cell_of(g, 0, p.x), cy = cell_of(g, 1, p.y), cz = cell_of(g, 2, p.z);
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    axis_setup(g, 0, o.x, d.x, inv.x, cx, 1, w.rx, w.stx, w.tnx, w.tdx);
+    axis_setup(g, 1, o.y, d.y, inv.y, cy, nx, w.ry, w.sty, w.tny, w.tdy);
+    axis_setup(g, 2, o.z, d.z, inv.z, cz, nx * ny, w.rz, w.stz, w.tnz, w.tdz);
     w.t1 = t1;
-    w.nx = g.n[0];
-    w.ny = g.n[1];
-    w.nz = g.n[2];
-    w.cell = (w.cz * w.ny + w.cy) * w.nx + w.cx;
-    w.left = w.nx + w.ny + w.nz + 3;
+    w.cell = (cz * ny + cy) * nx + cx;
+    w.left = nx + ny + nz + 3;
     return true;
 }
 
@@ -289,32 +289,28 @@ __device__ __forceinline__ R walk_cell_exit(const Walk<R>& w) {
 }
 
 // Step to the next cell (ties: x, then y, then z). False when the walk leaves
-// the grid or the clipped interval; sets *overflow past the step bound.
+// the grid or the clipped interval; sets *overflow past the step bound. Written
+// with selects rather than a branch per axis: the lanes of a warp step along
+// different axes.
 template <class R>
 __device__ __forceinline__ bool walk_next(Walk<R>& w, bool& overflow) {
     if (--w.left <= 0) {
         overflow = true;
         return false;
     }
-    if (w.tnx <= w.tny && w.tnx <= w.tnz) {
-        if (w.tnx > w.t1) return false;
-        w.cx += w.sx;
-        if ((unsigned)w.cx >= (unsigned)w.nx) return false;
-        w.tnx += w.tdx;
-        w.cell += w.sx;
-    } else if (w.tny <= w.tnz) {
-        if (w.tny > w.t1) return false;
-        w.cy += w.sy;
-        if ((unsigned)w.cy >= (unsigned)w.ny) return false;
-        w.tny += w.tdy;
-        w.cell += w.sy * w.nx;
-    } else {
-        if (w.tnz > w.t1) return false;
-        w.cz += w.sz;
-        if ((unsigned)w.cz >= (unsigned)w.nz) return false;
-        w.tnz += w.tdz;
-        w.cell += w.sz * w.nx * w.ny;
-    }
+    const bool bx = w.tnx <= w.tny && w.tnx <= w.tnz;
+    const bool by = !bx && w.tny <= w.tnz;
+    const bool bz = !bx && !by;
+    const R tn = bx ? w.tnx : (by ? w.tny : w.tnz);
+    const int r = bx ? w.rx : (by ? w.ry : w.rz);
+    if (tn > w.t1 || r <= 0) return false;
+    w.rx -= bx ? 1 : 0;
+    w.ry -= by ? 1 : 0;
+    w.rz -= bz ? 1 : 0;
+    w.tnx = bx ? w.tnx + w.tdx : w.tnx;
+    w.tny = by ? w.tny + w.tdy : w.tny;
+    w.tnz = bz ? w.tnz + w.tdz : w.tnz;
+    w.cell += bx ? w.stx : (by ? w.sty : w.stz);
     return true;
 }
 
