@@ -235,26 +235,19 @@ struct Walk {
     int left;
 };
 
+// One axis of the walk's set-up (selects, not branches: lanes differ in the
+// signs of their directions). Moving up the axis the next boundary is the
+// cell's upper face, moving down its lower face; a zero component never steps.
 template <class R>
 __device__ __forceinline__ void axis_setup(const GridDev& g, int k, R o, R d, R inv, int c, int stride, int& r,
                                            int& st, R& tn, R& td) {
-    R inf = Num<R>::inf();
-    if (d > R(0)) {
-        r = g.n[k] - 1 - c;
-        st = stride;
-        tn = (GridP<R>::lo(g, k) + R(c + 1) * GridP<R>::h(g, k) - o) * inv;
-        td = GridP<R>::h(g, k) * inv;
-    } else if (d < R(0)) {
-        r = c;
-        st = -stride;
-        tn = (GridP<R>::lo(g, k) + R(c) * GridP<R>::h(g, k) - o) * inv;
-        td = -GridP<R>::h(g, k) * inv;
-    } else {
-        r = 0;
-        st = 0;
-        tn = inf;
-        td = inf;
-    }
+    const bool up = d > R(0), down = d < R(0);
+    const R h = GridP<R>::h(g, k);
+    r = up ? g.n[k] - 1 - c : (down ? c : 0);
+    st = up ? stride : (down ? -stride : 0);
+    const R face = GridP<R>::lo(g, k) + R(up ? c + 1 : c) * h;
+    tn = (up || down) ? (face - o) * inv : Num<R>::inf();
+    td = (up || down) ? (up ? h : -h) * inv : Num<R>::inf();
 }
 
 template <class R>

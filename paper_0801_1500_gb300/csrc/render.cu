@@ -310,7 +310,7 @@ struct __align__(16) AoRay {
 //   mbox[lane]   direct-mapped ids this ray already tested (rows padded to 17
 //                words so distinct rays and slots fall in distinct banks); a
 //                re-test of a missed object cannot hit, so skipping it is exact
-//   qr/qid       surviving (ray, object) pairs waiting for a full test batch
+//   q            surviving (ray, object) pairs waiting for a full test batch
 constexpr int AO_MBOX = 8;
 // cells each active ray takes per lockstep iteration: further cells while it
 // holds fewer than AO_MIN_PAIRS candidates, at most AO_CELLS
@@ -324,13 +324,11 @@ struct AoWarp {
     // pairs start at or before p (split[g][r])
     unsigned delta[AO_CELLS][32];
     unsigned split[AO_CELLS][32];
-    uint32_t self[32];
     uint32_t owner[32];  // ray whose pairs start at this position of the current chunk
     uint32_t mbox[32][AO_MBOX + 1];
     ObjPtr<R> obj[32];
     const uint32_t* items[32];
-    uint32_t qid[64];
-    uint32_t qr[64];
+    uint2 q[64];  // queued pairs (ray lane, object id)
     uint2 fifo[32][AO_CELLS];  // cells a ray has loaded but not yet taken, oldest first
 };
 
@@ -340,8 +338,9 @@ struct AoWarp {
 template <class R>
 __device__ __forceinline__ unsigned ao_test_batch(AoWarp<R>& S, int lane, unsigned n) {
     const unsigned idx = (unsigned)lane < n ? (unsigned)lane : 0u;
-    const unsigned r = S.qr[idx];
-    const uint32_t id = S.qid[idx];
+    const uint2 e = S.q[idx];
+    const unsigned r = e.x;
+    const uint32_t id = e.y;
     const AoRay<R> ray = S.ray[r];
     R t;
     const bool hit = hit_object<R>(S.obj[r], id, ray.o, ray.d, R(0), ray.tmax, t) && (unsigned)lane < n;
@@ -431,9 +430,12 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
                         S.ray[lane] = ray;
                         S.obj[lane] = Obj<R>::base(F.scene);
                         S.items[lane] = F.grid.items;
-                        S.self[lane] = self;
 #pragma unroll
                         for (int m = 0; m < AO_MBOX; ++m) S.mbox[lane][m] = GBRT_MISS;
+                        // the own object starts in the mailbox: it is skipped like a
+                        // re-test while it stays there (testing it is harmless too --
+                        // behind a convex outer side the ray cannot meet it again)
+                        if (self != GBRT_MISS) S.mbox[lane][self & (AO_MBOX - 1)] = self;
                         nf = 0;
                         wend = false;
                         has = true;
@@ -545,23 +547,18 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
                 const uint32_t id = __ldg(S.items[r] + (p + di));
                 uint32_t* slot = &S.mbox[r][id & (AO_MBOX - 1)];
                 const uint32_t seen = *slot;
-                const bool keep = base + lane < T && id != S.self[r] && seen != id;
+                const bool keep = base + lane < T && seen != id;
                 const unsigned bal = __ballot_sync(FULL, keep);
                 if (keep) {
                     *slot = id;
-                    const unsigned q = qn + __popc(bal & lt);
-                    S.qr[q] = r;
-                    S.qid[q] = id;
+                    S.q[qn + __popc(bal & lt)] = make_uint2(r, id);
                 }
                 qn += __popc(bal);
                 __syncwarp();
                 if (qn >= 32) {
                     hitbits |= ao_test_batch(S, lane, 32u);
                     __syncwarp();
-                    if ((unsigned)lane < qn - 32) {
-                        S.qr[lane] = S.qr[32 + lane];
-                        S.qid[lane] = S.qid[32 + lane];
-                    }
+                    if ((unsigned)lane < qn - 32) S.q[lane] = S.q[32 + lane];
                     qn -= 32;
                     __syncwarp();
                 }
