@@ -316,6 +316,8 @@ constexpr int AO_MBOX = 8;
 // holds fewer than AO_MIN_PAIRS candidates, at most AO_CELLS
 constexpr int AO_CELLS = 4;
 constexpr unsigned AO_MIN_PAIRS = 6;
+// AO rays a warp claims from the global queue at once (its local pool)
+constexpr unsigned AO_CLAIM = 64;
 
 template <class R>
 struct AoWarp {
@@ -366,17 +368,26 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
     uint32_t lbit = 0;  // 0: an AO sample; 1 << l: the shadow ray toward light l
     int64_t vslot = 0;
     const uint2* cells = nullptr;
+    // the warp's pool of claimed rays [pool, pool_end) (warp-uniform)
+    unsigned long long pool = 0, pool_end = 0;
     while (true) {
-        // 1. compaction of rays: idle lanes take the next rays together
+        // 1. compaction of rays: idle lanes take the next rays together, from
+        //    the warp's pool, which claims AO_CLAIM more rays from the global
+        //    queue when it runs short (one atomic per AO_CLAIM rays)
         const unsigned act = __ballot_sync(FULL, has);
         if (!exhausted && __popc(act) < refill) {
             const unsigned idle = ~act;
-            unsigned long long base = 0;
-            if (lane == 0) base = atomicAdd(b.queue + 1, (unsigned long long)__popc(idle));
-            base = __shfl_sync(FULL, base, 0);
-            if (base >= total) exhausted = true;
+            const unsigned need = __popc(idle);
+            const unsigned long long rem = pool_end - pool;
+            unsigned long long fresh_base = 0;
+            if (rem < need) {
+                if (lane == 0) fresh_base = atomicAdd(b.queue + 1, (unsigned long long)AO_CLAIM);
+                fresh_base = __shfl_sync(FULL, fresh_base, 0);
+                if (fresh_base >= total) exhausted = true;
+            }
             if (!has) {
-                const unsigned long long jj = base + __popc(idle & lt);
+                const unsigned i = __popc(idle & lt);
+                const unsigned long long jj = i < rem ? pool + i : fresh_base + (i - rem);
                 if (jj < total) {
                     const int f = find_frame(b.job_off, b.nframes, jj);
                     const FrameDev& F = b.frames[f];
@@ -446,6 +457,12 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
                         atomicAdd(b.vis + vslot, 1u);
                     }
                 }
+            }
+            if (rem >= need) {
+                pool += need;
+            } else {
+                pool = fresh_base + (need - rem);
+                pool_end = fresh_base + AO_CLAIM;
             }
         }
         if (exhausted && __ballot_sync(FULL, has) == 0) break;
