@@ -62,46 +62,52 @@ __device__ __forceinline__ V3<float> view_dir_f(const FrameDev& f, uint32_t q) {
     return rsqrtf(dot(d, d)) * d;
 }
 
-// FP64 root of object `id`'s quadratic along o + t d by Newton's method from
-// an FP32 root t: F(t) = |f_p + t d_p|^2 - r^2 = A t^2 + 2 B t + C, with f_p
-// and d_p the parts of o - p0 and d perpendicular to the axis a (all of them
-// for a sphere, a = 0): A = d_p.d_p, B = f_p.d_p, C = f_p.f_p - r^2, and
-// F'(t) = 2 (A t + B). The coefficients are formed once in FP64 (their
-// cancellation near the root costs about |f_p|^2 / r of FP64's precision,
-// orders below the FP32 root's error). The steps divide by F' at the FP32
-// root, rounded to FP32 (a chord step: F' changes by a relative ~1e-7 over
-// the correction, so each step still gains ~7 digits) -- one FP32 reciprocal
-// and no further conversions. Two steps carry an FP32-accurate root to FP64
-// accuracy on non-grazing rays. False when the steps do not settle (a
-// grazing ray): the caller keeps the FP32 root.
-__device__ __forceinline__ bool newton_root64(const double2* obj64, uint32_t id, V3<double> o, V3<double> d,
-                                              double& t) {
-    V3<double> p0, a;
-    double L, r;
-    Obj<double>::load(obj64, id, p0, a, L, r);
-    const V3<double> f0 = o - p0;
-    const V3<double> fp = madd(f0, -dot(f0, a), a);
-    const V3<double> dp = madd(d, -dot(d, a), a);
-    const double A = dot(dp, dp), B = dot(fp, dp), C = fma(-r, r, dot(fp, fp));
-    const double B2 = 2.0 * B;
-    const double rFp = (double)__fdividef(1.0f, (float)fma(2.0 * A, t, B2));
-    double tt = t, corr = 0.0;
+// Refinement of an FP32 root in the object's own frame. The FP32 walk's root t
+// (along the FP64 ray o + t d) is turned into the hit's offset from the
+// object's base point p0 -- one FP64 point o + t d - p0, rounded to FP32; it
+// has the size of the object (|w| <= r + L), so FP32 holds it to ~1e-7 of
+// that -- and Newton steps in FP32 then move it along the ray by s to the
+// surface: F(s) = |w_p + s d_p|^2 - r^2 (w_p, d_p: the parts perpendicular to
+// the axis a; all of w and d for a sphere). The result is the offset w + s d
+// (the re-projection then needs no FP64 at all) and the root t + s in FP64
+// for ranking near-ties. False when the steps do not settle (a grazing ray):
+// the offset then stays at the FP32 root's point.
+struct LocalHit {
+    V3<float> w;  // hit point - p0
+    double t;     // root along the FP64 ray
+};
+
+__device__ __forceinline__ bool local_root(const SceneDev& sc, uint32_t id, V3<double> o, V3<double> d,
+                                           V3<float> df, double t, LocalHit& lh) {
+    const double2* q = sc.obj64 + 4 * (size_t)id;
+    const double2 q0 = __ldg(q), q1 = __ldg(q + 1);
+    V3<float> p0f, a;
+    float L, r;
+    Obj<float>::load(sc.obj, id, p0f, a, L, r);
+    const V3<float> w = to_f(madd(o, t, d) - v3(q0.x, q0.y, q1.x));
+    const float wa = dot(w, a), da = dot(df, a);
+    const V3<float> wp = madd(w, -wa, a), dp = madd(df, -da, a);
+    const float A = dot(dp, dp), B = dot(wp, dp), C = fmaf(-r, r, dot(wp, wp));
+    float s = 0.0f, corr = 0.0f;
 #pragma unroll
     for (int it = 0; it < 2; ++it) {
-        corr = fma(fma(A, tt, B2), tt, C) * rFp;
-        tt -= corr;
+        const float As = A * s;
+        corr = __fdividef(fmaf(As + 2.0f * B, s, C), 2.0f * (As + B));
+        s -= corr;
     }
-    const bool ok = fabs(corr) <= 1e-6 * (fabs(tt) + 1.0) && isfinite(tt);
-    if (ok) t = tt;
+    const bool ok = fabsf(corr) <= 1e-4f * (fabsf(s) + r) && isfinite(s);
+    if (!ok) s = 0.0f;
+    lh.w = madd(w, s, df);
+    lh.t = t + (double)s;
     return ok;
 }
 
 // FP32 path: nearest hit in FP32 from the FP32 ray re-based at the grid entry
 // (one FP64 point rounded once, so coordinates stay small relative to the
 // scene), then the winner -- and a runner-up within a relative 1e-4 band --
-// carried to its FP64 root (newton_root64) along the FP64 ray.
+// refined in its object's frame (local_root); the nearer refined root wins.
 __device__ __forceinline__ bool nearest_fp32_refined(const FrameDev& f, V3<double> o64, V3<double> d64,
-                                                     V3<float> df, uint32_t& id, double& t64, bool& overflow) {
+                                                     V3<float> df, uint32_t& id, LocalHit& lh, bool& overflow) {
     const float inf = Num<float>::inf();
     V3<float> of = to_f(o64);
     float te0, te1;
@@ -109,16 +115,14 @@ __device__ __forceinline__ bool nearest_fp32_refined(const FrameDev& f, V3<doubl
     V3<float> oe = to_f(madd(o64, (double)te0, d64));
     Nearest<float> h;
     if (!trace_nearest<float>(f.grid, f.scene, oe, df, 0.0f, inf, h, overflow)) return false;
-    double ta = (double)(te0 + h.t1);
-    newton_root64(f.scene.obj64, h.id1, o64, d64, ta);
+    local_root(f.scene, h.id1, o64, d64, df, (double)(te0 + h.t1), lh);
     id = h.id1;
-    t64 = ta;
     if (h.id2 != GBRT_MISS && (h.t2 - h.t1) <= 1e-4f * (h.t1 + te0)) {
-        double tb = (double)(te0 + h.t2);
-        newton_root64(f.scene.obj64, h.id2, o64, d64, tb);
-        if (tb < ta || (tb == ta && h.id2 < h.id1)) {
+        LocalHit l2;
+        local_root(f.scene, h.id2, o64, d64, df, (double)(te0 + h.t2), l2);
+        if (l2.t < lh.t || (l2.t == lh.t && h.id2 < h.id1)) {
             id = h.id2;
-            t64 = tb;
+            lh = l2;
         }
     }
     return true;
@@ -135,12 +139,12 @@ template <>
 struct HitIO<float> {
     static __device__ __forceinline__ void store(void* hits, int64_t slot, V3<double> o, V3<double> n, uint32_t q,
                                                  uint32_t id) {
-        store_f(hits, slot, o, to_f(n), q, id);
+        store_f(hits, slot, to_f(o), to_f(n), q, id);
     }
-    static __device__ __forceinline__ void store_f(void* hits, int64_t slot, V3<double> o, V3<float> n, uint32_t q,
+    static __device__ __forceinline__ void store_f(void* hits, int64_t slot, V3<float> o, V3<float> n, uint32_t q,
                                                    uint32_t id) {
         float4* H = (float4*)hits + 2 * slot;
-        H[0] = make_float4((float)o.x, (float)o.y, (float)o.z, __uint_as_float(q));
+        H[0] = make_float4(o.x, o.y, o.z, __uint_as_float(q));
         H[1] = make_float4(n.x, n.y, n.z, __uint_as_float(id));
     }
     static __device__ __forceinline__ void load(const void* hits, int64_t slot, V3<float>& o, V3<float>& n,
@@ -205,12 +209,13 @@ __global__ void __launch_bounds__(256) k_primary(const __grid_constant__ BatchDe
         V3<double> o64, d64;
         uint32_t id = GBRT_MISS;
         double t64 = 0.0;
+        LocalHit lh;
         bool hit = false;
         if (inside) {
             primary_ray64(F, i, j, o64, d64);
             if (MODE == GBRT_FP32) {
                 hit = nearest_fp32_refined(F, o64, d64, view_dir_f(F, (uint32_t)j * (uint32_t)F.W + (uint32_t)i),
-                                           id, t64, overflow);
+                                           id, lh, overflow);
             } else {
                 Nearest<double> h;
                 hit = trace_nearest<double>(F.grid, F.scene, o64, d64, 0.0, Num<double>::inf(), h, overflow);
@@ -231,22 +236,22 @@ __global__ void __launch_bounds__(256) k_primary(const __grid_constant__ BatchDe
         if (hit) {
             const int64_t slot = F.hit_base + base + __popc(hm & ((1u << lane) - 1u));
             if (MODE == GBRT_FP32) {
-                // FP64 hit point and its foot q on the generator (centre or
-                // axis); w_p = p - q has length r (to FP64 accuracy at the
-                // refined root), so the re-projected surface point plus eps
-                // along the normal facing the ray is q + (1 +- eps/r) w_p; the
-                // unit normal itself is needed in FP32 only
-                V3<double> p0, a;
-                double L, r;
-                Obj<double>::load(F.scene.obj64, id, p0, a, L, r);
-                const V3<double> w = madd(o64 - p0, t64, d64);
-                const double wa = dot(w, a);
-                const V3<double> wp = madd(w, -wa, a);
-                V3<float> nf = to_f(wp);
-                nf = rsqrtf(dot(nf, nf)) * nf;
+                // the refined offset w from p0 splits into its foot on the
+                // generator (centre or axis), p0 + (w.a) a, and w_p, the
+                // radial part (length r at the refined root); the re-projected
+                // surface point plus eps along the normal facing the ray is
+                // p0 + (w.a) a + (r +- eps) w_p/|w_p|, formed in FP32 relative
+                // to p0 and rounded once when p0 is added
+                V3<float> p0, a;
+                float L, r;
+                Obj<float>::load(F.scene.obj, id, p0, a, L, r);
+                const float wa = dot(lh.w, a);
+                const V3<float> wp = madd(lh.w, -wa, a);
+                const float inv = rsqrtf(dot(wp, wp));
+                V3<float> nf = inv * wp;
                 const bool flip = dot(view_dir_f(F, q), nf) > 0.0f;
-                const double er = (double)__fdividef(F.eps_f, (float)r);
-                const V3<double> ao_o = madd(madd(p0, wa, a), flip ? 1.0 - er : 1.0 + er, wp);
+                const V3<float> off = madd(wa * a, flip ? r - F.eps_f : r + F.eps_f, nf);
+                const V3<float> ao_o = p0 + off;
                 if (flip) nf = v3(-nf.x, -nf.y, -nf.z);
                 HitIO<float>::store_f(b.hits, slot, ao_o, nf, q | (flip ? HIT_INSIDE : 0u), id);
             } else {
