@@ -1,12 +1,12 @@
 """Benchmark: AO ray-tracing throughput (Mrays/s, fps) of the paper-sized scene.
 
 Default workload: the 26,318-object globule (13,500 spheres + 12,818 bonds)
-at 965x1137 with 16 AO samples per pixel, FP32 path with FP64 root and
-re-projection. A step renders one whole frame. Rays = primary rays (one per
+at 965x1137 with 16 AO samples per pixel, FP32 path (FP64 primary ray, hit
+refined in its object's frame). A step renders one whole frame. Rays = primary rays (one per
 pixel) + AO rays actually cast (samples x pixels whose primary ray hits).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload paper_1mp|paper_17mp|small] [--precision fp32|fp64]
+                  [--workload paper_1mp|paper_17mp|small|orbit64|serve] [--precision fp32|fp64]
 
 Under torchrun (N > 1) every rank renders its own frames (frames are
 independent; no collective on the data path): value = all ranks' rays / the

@@ -271,7 +271,7 @@ def default_lights() -> Lights:
                   intensity=[1.0, 1.0])
 
 
-PRECISION_FP32 = 0   # FP32 traversal/shading, FP64 root + re-projection
+PRECISION_FP32 = 0   # FP32 traversal/shading; FP64 ray, hit refined in its object's frame
 PRECISION_FP64 = 1   # plain FP64 throughout
 
 
