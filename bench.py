@@ -568,6 +568,10 @@ def main():
 
     props = torch.cuda.get_device_properties(dev)
     peaks, peak_src = measured_peaks()
+    # live calibration of the ALU roofline on this GPU at its current clock
+    calib = {"fp32_fma_tflops": round(G.gbrt_microbench(r.ctx, G.MB_FP32_FMA), 2),
+             "fp64_fma_tflops": round(G.gbrt_microbench(r.ctx, G.MB_FP64_FMA), 3),
+             "l2_read_gbs": round(G.gbrt_microbench(r.ctx, G.MB_L2_READ), 1)}
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
 
@@ -633,6 +637,8 @@ def main():
                     "traffic": committed_traffic(args.workload, args.precision),
                     "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 flop x "
                                    f"{sm_max:.0f} MHz ({peak_src} max clock)",
+                    "fma_measured_tflops": calib["fp32_fma_tflops"],
+                    "frac_of_measured_fma": round(achieved / calib["fp32_fma_tflops"], 4),
                     "kernel_ms": round(ao_s * 1e3, 4), "flops_per_ray": round(fpr, 1),
                     "walk_bytes_per_ray": round(bpr, 1), "walk_GBps": round(bpr * ao_rays / ao_s / 1e9, 1)}
 
@@ -649,7 +655,8 @@ def main():
             "config": config, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "phases_ms": ({k: round(sum(ph[k] for ph in phases) / len(phases), 4) for k in G.PHASES}
                           if phases else None),
-            "extras": extras or None, "wall_s_timed_region": round(wall, 4), "clocks": clk.summary()}
+            "extras": extras or None, "calibration": calib, "wall_s_timed_region": round(wall, 4),
+            "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
     r.close()
     if ws > 1:

@@ -269,9 +269,10 @@ GBRT_API int gbrt_scene_update(gbrt_ctx* ctx, gbrt_scene* scene, const float* sp
 /* gbrt_grid_rebuild: rebuild `grid` on the device for `scene`'s current
  * geometry (the scene it was built for: same object count, else
  * GBRT_EINVAL) with the grid's own cells-per-object density: scene box ->
- * cells per axis -> count -> exclusive scan -> scatter -> per-cell sort ->
- * bounding sphere, all on the context's stream; renders enqueued after it
- * use the new grid. The first call allocates buffers with headroom (cells
+ * cells per axis -> count -> exclusive scan -> scatter -> bounding sphere,
+ * all on the context's stream; renders enqueued after it use the new grid.
+ * The ids of a cell stay in scatter order (a host build sorts them; no
+ * render result depends on the order). The first call allocates buffers with headroom (cells
  * for 1.5x the target count, items for 1.5x the current references) and
  * waits for the stream once; later calls neither allocate nor wait, except
  * that a call which finds, from an earlier finished rebuild, that the items
@@ -367,6 +368,19 @@ GBRT_API int gbrt_set_profiling(gbrt_ctx* ctx, int on);
  * refinement, [1] AO plan, [2] AO shadow-ray walk, [3] shading. Waits for
  * that render. GBRT_EINVAL if no render was timed. */
 GBRT_API int gbrt_phase_times(gbrt_ctx* ctx, float ms[4]);
+
+/* Micro-benchmarks of the GPU the context runs on (not part of the paper's
+ * method: they calibrate the roofline the render kernels are compared with),
+ * timed with CUDA events on the context's stream at whatever clock the GPU
+ * runs; synchronises. *value receives
+ *   GBRT_MB_FP32_FMA  FP32 fused multiply-add rate, TFLOP/s (2 flop per FMA)
+ *   GBRT_MB_FP64_FMA  FP64 fused multiply-add rate, TFLOP/s
+ *   GBRT_MB_L2_READ   read bandwidth of a buffer of half the L2's size, GB/s
+ * GBRT_EINVAL for another kind; allocates (and frees) its own buffer. */
+#define GBRT_MB_FP32_FMA 0
+#define GBRT_MB_FP64_FMA 1
+#define GBRT_MB_L2_READ 2
+GBRT_API int gbrt_microbench(gbrt_ctx* ctx, int kind, double* value);
 
 /* Number of kernels this context has launched so far (host counter). */
 GBRT_API int64_t gbrt_launch_count(const gbrt_ctx* ctx);

@@ -356,6 +356,14 @@ GBRT_API int gbrt_grid_info(const gbrt_grid* grid, int32_t dims[3], float lo[3],
     return GBRT_OK;
 }
 
+GBRT_API int gbrt_microbench(gbrt_ctx* ctx, int kind, double* value) {
+    if (!ctx || !value) return GBRT_EINVAL;
+    if (kind != GBRT_MB_FP32_FMA && kind != GBRT_MB_FP64_FMA && kind != GBRT_MB_L2_READ) return GBRT_EINVAL;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return GBRT_EDEVICE;
+    return run_microbench(ctx, kind, value);
+}
+
 GBRT_API int gbrt_scene_update(gbrt_ctx* ctx, gbrt_scene* scene, const float* spheres, const float* cylinders,
                                int flags) {
     if (!ctx || !scene) return GBRT_EINVAL;

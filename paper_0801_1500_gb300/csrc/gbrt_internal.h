@@ -121,6 +121,7 @@ struct Grid {
     BuildAux* d_aux = nullptr;
     uint32_t* d_counts = nullptr;
     unsigned long long* d_sums = nullptr;
+    unsigned long long* d_reach = nullptr;  // per object: cells reached, from the count pass
     GridStat* d_stat = nullptr;
     GridStat* h_stat = nullptr;
     cudaEvent_t stat_ev = nullptr;
@@ -144,6 +145,8 @@ int grid_rebuild(Ctx* ctx, const Scene* s, Grid* g);
 int grid_refresh_host(Grid* g);
 // refresh a scene's host box after device-side updates (waits for `stream`)
 int scene_refresh_host(Scene* s, cudaStream_t stream);
+// microbench.cu: FMA rates (TFLOP/s) and L2 read bandwidth (GB/s) of the device
+int run_microbench(Ctx* ctx, int kind, double* value);
 
 // capi.cu: argument checks and the frame descriptor of one render
 int check_frame_args(const gbrt_scene* scene, const gbrt_grid* grid, const gbrt_camera* cam, int32_t W, int32_t H,

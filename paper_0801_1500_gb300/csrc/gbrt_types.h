@@ -33,7 +33,9 @@ struct SceneDev {
 };
 
 // Uniform grid. cells[c] = (first item, item count) of cell
-// c = (z * ny + y) * nx + x; items are global object ids, ascending per cell.
+// c = (z * ny + y) * nx + x; items are global object ids, ascending per cell
+// after a host build, in scatter order after a device-side rebuild (no result
+// depends on the order).
 struct GridDev {
     float lo[3], hi[3], h[3], inv_h[3];
     double lo64[3], hi64[3], h64[3], inv_h64[3];

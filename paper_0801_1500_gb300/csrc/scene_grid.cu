@@ -162,34 +162,49 @@ __device__ __forceinline__ bool cell_reached(const float4* obj, int64_t id, cons
     return box_dist2(A.x + sm * B.x, A.y + sm * B.y, A.z + sm * B.z, lo, hi) <= lim * lim;
 }
 
+// Count pass. When an object's box spans at most 64 cells, the cells its shape
+// reaches are also recorded as bits (x fastest, then y, then z) in reach[id],
+// so the scatter pass need not repeat the test; wider objects get all-ones
+// and are tested again there.
 __global__ void __launch_bounds__(256) k_grid_count(const float4* aabb, const float4* obj, int64_t N,
-                                                     const BuildP* bp, uint32_t* counts) {
+                                                     const BuildP* bp, uint32_t* counts,
+                                                     unsigned long long* reach) {
     int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= N) return;
     const BuildP p = *bp;
     int c0[3], c1[3];
     cell_range(aabb, id, p, c0, c1);
+    const int span = (c1[0] - c0[0] + 1) * (c1[1] - c0[1] + 1) * (c1[2] - c0[2] + 1);
+    unsigned long long bits = 0ull;
+    int k = 0;
     for (int z = c0[2]; z <= c1[2]; ++z)
         for (int y = c0[1]; y <= c1[1]; ++y)
-            for (int x = c0[0]; x <= c1[0]; ++x)
-                if (cell_reached(obj, id, p, x, y, z))
+            for (int x = c0[0]; x <= c1[0]; ++x, ++k)
+                if (cell_reached(obj, id, p, x, y, z)) {
                     atomicAdd(counts + ((int64_t)z * p.n[1] + y) * p.n[0] + x, 1u);
+                    if (k < 64) bits |= 1ull << k;
+                }
+    reach[id] = span <= 64 ? bits : ~0ull;
 }
 
 // Items past `items_cap` are dropped (a device-side rebuild that outgrew its
 // buffer; its finish step then disables the grid and flags the error).
 __global__ void __launch_bounds__(256) k_grid_scatter(const float4* aabb, const float4* obj, int64_t N,
-                                                       const BuildP* bp, const uint2* cells, uint32_t* cursor,
-                                                       uint32_t* items, uint64_t items_cap) {
+                                                       const BuildP* bp, const unsigned long long* reach,
+                                                       const uint2* cells, uint32_t* cursor, uint32_t* items,
+                                                       uint64_t items_cap) {
     int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= N) return;
     const BuildP p = *bp;
     int c0[3], c1[3];
     cell_range(aabb, id, p, c0, c1);
+    const unsigned long long bits = reach[id];
+    const bool recorded = bits != ~0ull;
+    int k = 0;
     for (int z = c0[2]; z <= c1[2]; ++z)
         for (int y = c0[1]; y <= c1[1]; ++y)
-            for (int x = c0[0]; x <= c1[0]; ++x) {
-                if (!cell_reached(obj, id, p, x, y, z)) continue;
+            for (int x = c0[0]; x <= c1[0]; ++x, ++k) {
+                if (recorded ? !((bits >> k) & 1ull) : !cell_reached(obj, id, p, x, y, z)) continue;
                 int64_t c = ((int64_t)z * p.n[1] + y) * p.n[0] + x;
                 uint32_t slot = atomicAdd(cursor + c, 1u);
                 const uint64_t at = (uint64_t)cells[c].x + slot;
@@ -456,6 +471,7 @@ void grid_release(Grid* g) {
     cudaFree(g->d_aux);
     cudaFree(g->d_counts);
     cudaFree(g->d_sums);
+    cudaFree(g->d_reach);
     cudaFree(g->d_stat);
     cudaFreeHost(g->h_stat);
     if (g->stat_ev) cudaEventDestroy(g->stat_ev);
@@ -590,6 +606,7 @@ __global__ void k_grid_finish(GridDev* geom, const BuildAux* aux, const unsigned
 int grid_build(Ctx* ctx, const Scene* s, float lambda, Grid* g) {
     int rc = GBRT_OK;
     uint32_t* counts = nullptr;
+    unsigned long long* reach = nullptr;
     uint32_t* cursor = nullptr;
     unsigned long long* sums = nullptr;
     unsigned long long h_total = 0;
@@ -609,6 +626,7 @@ int grid_build(Ctx* ctx, const Scene* s, float lambda, Grid* g) {
         const int64_t nc = d.ncells;
         GB_TRY(cudaMalloc(&g->cells, (size_t)nc * sizeof(uint2)));
         GB_TRY(cudaMalloc(&counts, (size_t)nc * sizeof(uint32_t)));
+        GB_TRY(cudaMalloc(&reach, (size_t)std::max<int64_t>(N, 1) * sizeof(unsigned long long)));
         GB_TRY(cudaMemsetAsync(counts, 0, (size_t)nc * sizeof(uint32_t), ctx->stream));
         const int64_t nb = (nc + SCAN_TILE - 1) / SCAN_TILE;
         // sums: nb block sums, total, then the build parameters
@@ -616,7 +634,8 @@ int grid_build(Ctx* ctx, const Scene* s, float lambda, Grid* g) {
         BuildAux* d_aux = (BuildAux*)(sums + nb + 2);
         GB_TRY(cudaMemcpyAsync(d_aux, &a, sizeof(a), cudaMemcpyHostToDevice, ctx->stream));
         if (N > 0) {
-            k_grid_count<<<(int)((N + 255) / 256), 256, 0, ctx->stream>>>(s->aabb, s->obj, N, &d_aux->p, counts);
+            k_grid_count<<<(int)((N + 255) / 256), 256, 0, ctx->stream>>>(s->aabb, s->obj, N, &d_aux->p, counts,
+                                                                          reach);
             k_bound_radius<<<(int)((N + 255) / 256), 256, 0, ctx->stream>>>(s->obj64, N, d_aux->ctr, &d_aux->rbits);
             ctx->launches += 2;
             GB_TRY(cudaGetLastError());
@@ -639,7 +658,8 @@ int grid_build(Ctx* ctx, const Scene* s, float lambda, Grid* g) {
         if (N > 0) {
             cursor = counts;  // reuse as per-cell fill cursor
             GB_TRY(cudaMemsetAsync(cursor, 0, (size_t)nc * sizeof(uint32_t), ctx->stream));
-            k_grid_scatter<<<(int)((N + 255) / 256), 256, 0, ctx->stream>>>(s->aabb, s->obj, N, &d_aux->p, g->cells,
+            k_grid_scatter<<<(int)((N + 255) / 256), 256, 0, ctx->stream>>>(s->aabb, s->obj, N, &d_aux->p, reach,
+                                                                            g->cells,
                                                                             cursor, g->items, (uint64_t)g->refs);
             k_cell_sort<<<(int)((nc + 255) / 256), 256, 0, ctx->stream>>>(g->cells, nc, g->items,
                                                                           (uint64_t)g->refs);
@@ -652,11 +672,13 @@ int grid_build(Ctx* ctx, const Scene* s, float lambda, Grid* g) {
         g->bytes = (size_t)nc * sizeof(uint2) + (size_t)std::max<int64_t>(g->refs, 1) * sizeof(uint32_t);
     }
     cudaFree(counts);
+    cudaFree(reach);
     cudaFree(sums);
     return GBRT_OK;
 fail:
     cudaStreamSynchronize(ctx->stream);
     cudaFree(counts);
+    cudaFree(reach);
     cudaFree(sums);
     grid_release(g);
     return rc;
@@ -748,6 +770,7 @@ int grid_rebuild(Ctx* ctx, const Scene* s, Grid* g) {
         if (cudaMalloc(&g->d_geom, sizeof(GridDev)) != cudaSuccess ||
             cudaMalloc(&g->d_aux, sizeof(BuildAux)) != cudaSuccess ||
             cudaMalloc(&g->d_stat, sizeof(GridStat)) != cudaSuccess ||
+            cudaMalloc(&g->d_reach, (size_t)std::max<int64_t>(N, 1) * sizeof(unsigned long long)) != cudaSuccess ||
             cudaMallocHost(&g->h_stat, sizeof(GridStat)) != cudaSuccess ||
             cudaEventCreateWithFlags(&g->stat_ev, cudaEventDisableTiming) != cudaSuccess)
             return GBRT_ENOMEM;
@@ -780,7 +803,7 @@ int grid_rebuild(Ctx* ctx, const Scene* s, Grid* g) {
     if (cudaMemsetAsync(g->d_counts, 0, (size_t)nc * sizeof(uint32_t), st) != cudaSuccess) return GBRT_EDEVICE;
     k_grid_geometry<<<1, 32, 0, st>>>(s->d_box, N, g->lambda, nc, g->cells, g->items, g->d_geom, g->d_aux);
     if (N > 0) {
-        k_grid_count<<<blocksN, 256, 0, st>>>(s->aabb, s->obj, N, &g->d_aux->p, g->d_counts);
+        k_grid_count<<<blocksN, 256, 0, st>>>(s->aabb, s->obj, N, &g->d_aux->p, g->d_counts, g->d_reach);
         k_bound_radius<<<blocksN, 256, 0, st>>>(s->obj64, N, g->d_aux->ctr, &g->d_aux->rbits);
     }
     k_scan_reduce<<<(int)nb, SCAN_T, 0, st>>>(g->d_counts, nc, g->d_sums);
@@ -788,13 +811,15 @@ int grid_rebuild(Ctx* ctx, const Scene* s, Grid* g) {
     k_scan_apply<<<(int)nb, SCAN_T, 0, st>>>(g->d_counts, nc, g->d_sums, g->cells);
     if (N > 0) {
         if (cudaMemsetAsync(g->d_counts, 0, (size_t)nc * sizeof(uint32_t), st) != cudaSuccess) return GBRT_EDEVICE;
-        k_grid_scatter<<<blocksN, 256, 0, st>>>(s->aabb, s->obj, N, &g->d_aux->p, g->cells, g->d_counts, g->items,
+        k_grid_scatter<<<blocksN, 256, 0, st>>>(s->aabb, s->obj, N, &g->d_aux->p, g->d_reach, g->cells, g->d_counts,
+                                                g->items,
                                                 (uint64_t)g->items_cap);
-        k_cell_sort<<<(int)((nc + 255) / 256), 256, 0, st>>>(g->cells, nc, g->items, (uint64_t)g->items_cap);
+        // no per-cell sort: no result depends on the order of a cell's ids
+        // (nearest hits rank by (t, id), any-hit queries OR their tests)
     }
     k_grid_finish<<<1, 32, 0, st>>>(g->d_geom, g->d_aux, g->d_sums + nb, (unsigned long long)g->items_cap, g->d_stat,
                                     ctx->d_err);
-    ctx->launches += N > 0 ? 9 : 5;
+    ctx->launches += N > 0 ? 8 : 5;
     if (cudaGetLastError() != cudaSuccess) return GBRT_EDEVICE;
     if (cudaMemcpyAsync(g->h_stat, g->d_stat, sizeof(GridStat), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaEventRecord(g->stat_ev, st) != cudaSuccess)

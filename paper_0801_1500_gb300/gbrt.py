@@ -81,6 +81,7 @@ def _load():
         "gbrt_grid_info": ([P, P, P, P, P, P], C.c_int),
         "gbrt_grid_free": ([P, P], C.c_int),
         "gbrt_scene_update": ([P, P, P, P, C.c_int], C.c_int),
+        "gbrt_microbench": ([P, C.c_int, C.POINTER(C.c_double)], C.c_int),
         "gbrt_grid_rebuild": ([P, P, P], C.c_int),
         "gbrt_render": ([P, P, P, C.POINTER(gbrt_camera), i32, i32, i32, C.POINTER(gbrt_lights),
                          C.POINTER(gbrt_params), P, P, P], C.c_int),
@@ -253,6 +254,16 @@ def gbrt_scene_update(ctx, scene, spheres, cylinders, flags=None):
                 and cylinders.flags.c_contiguous):
             cylinders = np.ascontiguousarray(cylinders, np.float32)
     return _check(lib.gbrt_scene_update(ctx, scene, ptr(spheres), ptr(cylinders), int(flags)), "gbrt_scene_update")
+
+
+MB_FP32_FMA, MB_FP64_FMA, MB_L2_READ = 0, 1, 2
+
+
+def gbrt_microbench(ctx, kind):
+    """FMA rate (TFLOP/s) or L2 read bandwidth (GB/s) of the context's GPU."""
+    v = C.c_double()
+    _check(lib.gbrt_microbench(ctx, int(kind), C.byref(v)), "gbrt_microbench")
+    return v.value
 
 
 def gbrt_grid_rebuild(ctx, grid, scene):
