@@ -77,23 +77,32 @@ def sources_hash():
     return h.hexdigest()[:16]
 
 
-def committed_traffic(workload_name, precision):
-    """DRAM bytes per launch of the AO walk kernel from the committed ncu
-    summary, if it was taken on the current kernel sources (else None)."""
+def committed_profile(workload_name, precision):
+    """Figures of the AO walk kernel from the committed ncu summary, if it was
+    taken on the current kernel sources (else {})."""
     p = os.path.join(ROOT, "profiles", f"k_ao_walk_{precision}_{workload_name}.txt")
     if not os.path.exists(p):
-        return None
+        return {}
     kv = {}
     for line in open(p):
-        if ":" in line:
+        if ":" in line and not line.startswith("#"):
             k, v = line.split(":", 1)
             kv[k.strip()] = v.strip()
     if kv.get("sources_hash") != sources_hash():
-        return None
-    try:
-        return float(kv["dram_bytes_per_launch"])
-    except (KeyError, ValueError):
-        return None
+        return {}
+    out = {}
+    for key in ("dram_bytes_per_launch", "issue_active_pct"):
+        try:
+            out[key] = float(kv[key])
+        except (KeyError, ValueError):
+            pass
+    return out
+
+
+def committed_traffic(workload_name, precision):
+    """DRAM bytes per launch of the AO walk kernel from the committed ncu
+    summary, if it was taken on the current kernel sources (else None)."""
+    return committed_profile(workload_name, precision).get("dram_bytes_per_launch")
 
 
 def measured_peaks():
@@ -632,11 +641,14 @@ def main():
             ao_rays = rays_per_step - W * H
             ao_s = sum(ph["ao_walk"] for ph in phases) / len(phases) / 1e3
             achieved = fpr * ao_rays / ao_s / 1e12
+            prof = committed_profile(args.workload, args.precision)
             roof = {"bound": "alu", "kernel": "k_ao_walk", "achieved": round(achieved, 3),
                     "peak": round(fp32_peak, 2), "unit": "TFLOP/s", "frac": round(achieved / fp32_peak, 4),
                     "traffic": committed_traffic(args.workload, args.precision),
                     "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 flop x "
                                    f"{sm_max:.0f} MHz ({peak_src} max clock)",
+                    "issue_slots_busy_ncu": (round(prof["issue_active_pct"] / 100.0, 3)
+                                             if "issue_active_pct" in prof else None),
                     "fma_measured_tflops": calib["fp32_fma_tflops"],
                     "frac_of_measured_fma": round(achieved / calib["fp32_fma_tflops"], 4),
                     "kernel_ms": round(ao_s * 1e3, 4), "flops_per_ray": round(fpr, 1),
