@@ -2,12 +2,13 @@
  * gbrt.h -- C ABI of the GB300 molecular ambient-occlusion ray tracer.
  *
  * The library renders molecular scenes of spheres (atoms) and open cylinders
- * (bonds) the way the paper's Tachyon runs do (Sec. 2: "-res W H -trans_vmd
- * -rescale_lights 0.3 -add_skylight 1.0"): one primary ray per pixel, its
- * nearest hit, Monte-Carlo ambient-occlusion shadow rays from the hit point,
- * then Phong shading under rescaled directional lights plus an AO-weighted
- * skylight. Rays walk a uniform grid built on the device (Table 5's
- * "Preprocess" phase). Every step runs in CUDA kernels compiled for sm_103a.
+ * (bonds) the way the paper's Tachyon runs do (Sec. 2: a given image size,
+ * ambient occlusion on, lights rescaled by 0.3, a skylight of 1.0): one primary
+ * ray per pixel, its nearest hit, Monte-Carlo ambient-occlusion shadow rays
+ * from the hit point, then Phong shading under rescaled directional lights plus
+ * an AO-weighted skylight. Rays walk a uniform grid built on the device (the
+ * preprocessing phase of Table 5). Every step runs in CUDA kernels compiled for
+ * sm_103a.
  *
  * Conventions for every entry point:
  *  - Return value: GBRT_OK (0) or a negative GBRT_E* code; nothing throws.
@@ -59,7 +60,7 @@ extern "C" {
 
 /* ---- precision ---- */
 #define GBRT_FP32 0  /* FP32 traversal, intersection and shading; FP64 ray, hit refined in its object's frame */
-#define GBRT_FP64 1  /* FP64 throughout (the paper's "double precision", Sec. 2) */
+#define GBRT_FP64 1  /* FP64 throughout (the paper's all-double-precision build, Sec. 2) */
 
 #define GBRT_CAMERA_ORTHO 0
 #define GBRT_CAMERA_PINHOLE 1

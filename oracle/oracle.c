@@ -8,13 +8,13 @@
  * arrays and parameter values, nothing else.
  *
  * What it computes, and where each step comes from:
- *  - The paper (Sec. 2) renders with Tachyon compiled "double precision for all
- *    calculations", at -res W H, with ambient occlusion ("Monte Carlo sampling
- *    of illumination"), -rescale_lights 0.3 and -add_skylight 1.0. Everything
- *    here is in double precision with libm.
+ *  - The paper (Sec. 2) renders with a Tachyon build whose arithmetic is all
+ *    double precision, at -res W H, with ambient occlusion computed by random
+ *    sampling of the incoming light, -rescale_lights 0.3 and -add_skylight 1.0.
+ *    Everything here is in double precision with libm.
  *  - The paper does not spell out the tracer's algorithms. The readings used
- *    (camera, materials, epsilon, sampling map) are listed in the design notes
- *    and are passed in as parameters; this file implements:
+ *    (camera, materials, epsilon, sampling map) come in as parameters; this
+ *    file implements:
  *      * nearest hit = the smallest t over ALL objects (brute force is the
  *        definition); equal t -> smaller global id (spheres 0..S-1, then
  *        cylinders S..S+C-1);
