@@ -737,22 +737,33 @@ int scene_update(Ctx* ctx, Scene* s, const float* spheres, const float* cyl, int
     return cudaGetLastError() == cudaSuccess ? GBRT_OK : GBRT_EDEVICE;
 }
 
+// Buffers of a device-side rebuild: cells, counts and scan sums for cells_cap,
+// items for items_cap. All or nothing: on failure the grid keeps its previous
+// buffers (and stays usable); the caller has drained the stream.
 static int dyn_alloc(Grid* g, int64_t cells_cap, int64_t items_cap) {
-    // cells, counts, scan sums sized for cells_cap; items for items_cap
+    const int64_t nb = (cells_cap + SCAN_TILE - 1) / SCAN_TILE;
+    uint2* cells = nullptr;
+    uint32_t* items = nullptr;
+    uint32_t* counts = nullptr;
+    unsigned long long* sums = nullptr;
+    if (cudaMalloc(&cells, (size_t)cells_cap * sizeof(uint2)) != cudaSuccess ||
+        cudaMalloc(&items, (size_t)items_cap * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMalloc(&counts, (size_t)cells_cap * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMalloc(&sums, (size_t)(nb + 2) * sizeof(unsigned long long)) != cudaSuccess) {
+        cudaFree(cells);
+        cudaFree(items);
+        cudaFree(counts);
+        cudaFree(sums);
+        return GBRT_ENOMEM;
+    }
     cudaFree(g->cells);
     cudaFree(g->items);
     cudaFree(g->d_counts);
     cudaFree(g->d_sums);
-    g->cells = nullptr;
-    g->items = nullptr;
-    g->d_counts = nullptr;
-    g->d_sums = nullptr;
-    const int64_t nb = (cells_cap + SCAN_TILE - 1) / SCAN_TILE;
-    if (cudaMalloc(&g->cells, (size_t)cells_cap * sizeof(uint2)) != cudaSuccess ||
-        cudaMalloc(&g->items, (size_t)items_cap * sizeof(uint32_t)) != cudaSuccess ||
-        cudaMalloc(&g->d_counts, (size_t)cells_cap * sizeof(uint32_t)) != cudaSuccess ||
-        cudaMalloc(&g->d_sums, (size_t)(nb + 2) * sizeof(unsigned long long)) != cudaSuccess)
-        return GBRT_ENOMEM;
+    g->cells = cells;
+    g->items = items;
+    g->d_counts = counts;
+    g->d_sums = sums;
     g->cells_cap = cells_cap;
     g->items_cap = items_cap;
     g->bytes = (size_t)cells_cap * (sizeof(uint2) + sizeof(uint32_t)) + (size_t)items_cap * sizeof(uint32_t);
@@ -767,20 +778,27 @@ int grid_rebuild(Ctx* ctx, const Scene* s, Grid* g) {
     int rc = GBRT_OK;
     if (!g->dynamic) {
         // first device-side rebuild: buffers with headroom for moving geometry
-        if (cudaMalloc(&g->d_geom, sizeof(GridDev)) != cudaSuccess ||
-            cudaMalloc(&g->d_aux, sizeof(BuildAux)) != cudaSuccess ||
-            cudaMalloc(&g->d_stat, sizeof(GridStat)) != cudaSuccess ||
-            cudaMalloc(&g->d_reach, (size_t)std::max<int64_t>(N, 1) * sizeof(unsigned long long)) != cudaSuccess ||
-            cudaMallocHost(&g->h_stat, sizeof(GridStat)) != cudaSuccess ||
-            cudaEventCreateWithFlags(&g->stat_ev, cudaEventDisableTiming) != cudaSuccess)
+        // (a retry after a failure reuses what an earlier attempt allocated)
+        if ((!g->d_geom && cudaMalloc(&g->d_geom, sizeof(GridDev)) != cudaSuccess) ||
+            (!g->d_aux && cudaMalloc(&g->d_aux, sizeof(BuildAux)) != cudaSuccess) ||
+            (!g->d_stat && cudaMalloc(&g->d_stat, sizeof(GridStat)) != cudaSuccess) ||
+            (!g->d_reach &&
+             cudaMalloc(&g->d_reach, (size_t)std::max<int64_t>(N, 1) * sizeof(unsigned long long)) != cudaSuccess) ||
+            (!g->h_stat && cudaMallocHost(&g->h_stat, sizeof(GridStat)) != cudaSuccess) ||
+            (!g->stat_ev && cudaEventCreateWithFlags(&g->stat_ev, cudaEventDisableTiming) != cudaSuccess))
             return GBRT_ENOMEM;
         cudaStreamSynchronize(ctx->stream);  // renders may still read the host-built arrays
         const int64_t target = (int64_t)std::min(std::max((double)g->lambda * (double)N, 1.0), 67108864.0);
         const int64_t cells_cap = std::max<int64_t>(g->dev.ncells, target + target / 2) + 4096;
         const int64_t items_cap = std::max<int64_t>(g->refs + g->refs / 2, 4096);
         if ((rc = dyn_alloc(g, cells_cap, items_cap)) != GBRT_OK) return rc;
-        if (cudaMemcpy(g->d_geom, &g->dev, sizeof(GridDev), cudaMemcpyHostToDevice) != cudaSuccess)
+        if (cudaMemcpy(g->d_geom, &g->dev, sizeof(GridDev), cudaMemcpyHostToDevice) != cudaSuccess) {
+            // the new buffers hold no lists yet: leave the grid unusable (renders
+            // reject it) until a rebuild succeeds
+            g->dev.cells = nullptr;
+            g->dev.items = nullptr;
             return GBRT_EDEVICE;
+        }
         g->dynamic = true;
     } else if (g->stat_pending && cudaEventQuery(g->stat_ev) == cudaSuccess) {
         // the last finished rebuild's reference count: grow the item buffer
