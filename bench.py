@@ -19,6 +19,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import math
 import os
@@ -68,12 +69,21 @@ def dist_env():
 KERNEL_SOURCES = ("gbrt_device.cuh", "gbrt_types.h", "render.cu")
 
 
+def _code_only(text):
+    """C++ source without its comments and blank space (comment edits do not
+    change a kernel)."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def sources_hash():
-    """Hash of the sources that define the render kernels."""
+    """Hash of the code (comments stripped) of the sources that define the
+    render kernels."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_0801_1500_gb300", "csrc")
     for f in KERNEL_SOURCES:
-        h.update(open(os.path.join(d, f), "rb").read())
+        h.update(_code_only(open(os.path.join(d, f)).read()).encode())
     return h.hexdigest()[:16]
 
 

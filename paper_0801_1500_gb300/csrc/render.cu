@@ -311,11 +311,18 @@ struct __align__(16) AoRay {
 };
 
 // Per-warp shared state of the cooperative AO walk.
-//   excl/first   the scan of the lanes' candidate counts and their first items
-//   mbox[lane]   direct-mapped ids this ray already tested (rows padded to 17
-//                words so distinct rays and slots fall in distinct banks); a
-//                re-test of a missed object cannot hit, so skipping it is exact
-//   q            surviving (ray, object) pairs waiting for a full test batch
+//   ray[lane]      the lane's ray (origin, tmax, direction)
+//   delta, split   where each ray's pairs of the current iteration find their
+//                  items (one range per cell taken)
+//   owner          the ray whose pairs start at a position of the current chunk
+//   mbox[lane]     direct-mapped ids this ray already tested (rows padded to
+//                  AO_MBOX + 1 words so distinct rays and slots fall in
+//                  distinct banks); a re-test of a missed object cannot hit,
+//                  so skipping it is exact
+//   obj, items     the ray's scene records and grid item list (batches mix
+//                  scenes)
+//   q              surviving (ray, object) pairs waiting for a full test batch
+//   fifo[lane]     cells the ray has stepped to and loaded but not yet taken
 constexpr int AO_MBOX = 8;
 // cells each active ray takes per lockstep iteration: further cells while it
 // holds fewer than AO_MIN_PAIRS candidates, at most AO_CELLS
