@@ -56,6 +56,7 @@ extern "C" {
 /* ---- flags ---- */
 #define GBRT_DEVICE_PTRS 0
 #define GBRT_HOST_PTRS 1      /* array arguments are host memory */
+#define GBRT_HOST_ASYNC 4     /* with GBRT_HOST_PTRS: host outputs are filled asynchronously */
 #define GBRT_BATCH_GRAPH 2    /* gbrt_render_batch: replay through a CUDA graph */
 
 /* ---- precision ---- */
@@ -128,7 +129,13 @@ typedef struct gbrt_lights {
  *              light the surface faces; any hit (0 < t) drops that light's
  *              diffuse and specular terms. 0: lights are never blocked
  *  out_flags   GBRT_HOST_PTRS: the render's output pointers are host memory
- *              (the call then synchronises). */
+ *              (the call then synchronises). GBRT_HOST_PTRS | GBRT_HOST_ASYNC:
+ *              host outputs too, but the call returns once the copies are
+ *              enqueued; the outputs are complete, and device-side errors
+ *              reported, at the next gbrt_sync. Page-locked host memory makes
+ *              the copies truly asynchronous; successive calls are ordered on
+ *              the context's stream, so a stream of frames runs without a
+ *              host round trip per frame. */
 typedef struct gbrt_params {
     int32_t precision;
     int32_t out_flags;

@@ -400,10 +400,12 @@ GBRT_API int gbrt_render(gbrt_ctx* ctx, const gbrt_scene* scene, const gbrt_grid
     if (!ctx) return GBRT_EINVAL;
     int rc = check_frame_args(scene, grid, camera, width, height, ao_samples, lights, params, out_rgb);
     if (rc != GBRT_OK) return rc;
-    if (params->out_flags & ~GBRT_HOST_PTRS) return GBRT_EINVAL;
+    if (params->out_flags & ~(GBRT_HOST_PTRS | GBRT_HOST_ASYNC)) return GBRT_EINVAL;
+    if ((params->out_flags & GBRT_HOST_ASYNC) && !(params->out_flags & GBRT_HOST_PTRS)) return GBRT_EINVAL;
     DeviceGuard g(ctx->device);
     if (!g.ok) return GBRT_EDEVICE;
     const bool host = (params->out_flags & GBRT_HOST_PTRS) != 0;
+    const bool async = (params->out_flags & GBRT_HOST_ASYNC) != 0;
     const size_t aa = camera->aa > 1 ? (size_t)camera->aa : 1;
     const size_t rgb_bytes =
         (size_t)width * height * 3 * (params->precision == GBRT_FP64 ? sizeof(double) : sizeof(float));
@@ -434,7 +436,7 @@ GBRT_API int gbrt_render(gbrt_ctx* ctx, const gbrt_scene* scene, const gbrt_grid
         if (e == cudaSuccess && out_ao_visible)
             e = cudaMemcpyAsync(out_ao_visible, d_vis, npx * 4, cudaMemcpyDeviceToHost, ctx->stream);
         if (e != cudaSuccess) return err_of(e);
-        return read_error_word(ctx);
+        return async ? GBRT_OK : read_error_word(ctx);
     }
     return GBRT_OK;
 }

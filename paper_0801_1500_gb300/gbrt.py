@@ -18,7 +18,7 @@ from . import build as _build
 LIB_PATH = _build.LIB
 
 OK, EINVAL, ENOMEM, EDEVICE, ETIMEDOUT, ETRAVERSAL, ECAPACITY = 0, -1, -2, -3, -4, -5, -6
-DEVICE_PTRS, HOST_PTRS, BATCH_GRAPH = 0, 1, 2
+DEVICE_PTRS, HOST_PTRS, BATCH_GRAPH, HOST_ASYNC = 0, 1, 2, 4
 FP32, FP64 = 0, 1
 CAMERA_ORTHO, CAMERA_PINHOLE = 0, 1
 MAX_LIGHTS = 8

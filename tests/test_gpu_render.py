@@ -232,6 +232,33 @@ def test_host_output_pointers(G, R):
     R.free(scene, grid)
 
 
+def test_asynchronous_host_outputs(G, R):
+    # three frames enqueued back to back into page-locked host buffers, one
+    # wait at the end: each equals its synchronous render
+    import torch
+    sc = S.globule(300, 285, 10.0, seed=9)
+    W, H = 70, 50
+    cam = S.ortho_camera(sc, W, H)
+    scene, grid = R.upload(sc)
+    frames = [S.Params(ao_samples=6, seed=s, frame=s) for s in (1, 2, 3)]
+    outs = [(torch.empty((H, W, 3), dtype=torch.float32).pin_memory().numpy(),
+             torch.empty((H, W), dtype=torch.int32).pin_memory().numpy().view(np.uint32)) for _ in frames]
+    for p, (rgb, ids) in zip(frames, outs):
+        G.gbrt_render(R.ctx, scene, grid, cam, W, H, 6, S.default_lights(),
+                      G.make_params(p, out_flags=G.HOST_PTRS | G.HOST_ASYNC), rgb, ids)
+    G.gbrt_sync(R.ctx)
+    for p, (rgb, ids) in zip(frames, outs):
+        ref_rgb, ref_ids = np.zeros((H, W, 3), np.float32), np.zeros((H, W), np.uint32)
+        G.gbrt_render(R.ctx, scene, grid, cam, W, H, 6, S.default_lights(), G.make_params(p, out_flags=G.HOST_PTRS),
+                      ref_rgb, ref_ids)
+        assert np.array_equal(rgb, ref_rgb) and np.array_equal(ids, ref_ids)
+    assert not np.array_equal(outs[0][0], outs[1][0])  # different seeds, different AO
+    with pytest.raises(G.GbrtError):  # asynchronous outputs must be host outputs
+        G.gbrt_render(R.ctx, scene, grid, cam, W, H, 6, S.default_lights(),
+                      G.make_params(frames[0], out_flags=G.HOST_ASYNC), torch.empty((H, W, 3), device="cuda"))
+    R.free(scene, grid)
+
+
 def test_deterministic_and_grid_invariant(G, R):
     sc = S.globule(800, 760, 16.0, seed=5)
     W, H = 120, 90
