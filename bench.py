@@ -373,12 +373,12 @@ def run_serve(args):
            "dtype": "f32" if prec == S.PRECISION_FP32 else "f64",
            "config": {"workload": "serve_8scenes_1k-250k_poisson", "objects": [s.n_objects for s in scenes],
                       "resolutions": S.SERVE_RESOLUTIONS, "spp": S.SERVE_SPP, "hbm_budget_GB": args.hbm_gb,
-                      "grid_lambda": args.lam or 2.0}}
+                      "grid_lambda": args.lam or 8.0}}
     with ClockSampler(local) as clk:
         # the offered stream at several rates (the highest is the configured rate)
         sweep = []
         for rate in args.rates:
-            be = SV.GpuBackend(local, lam=args.lam or 2.0)
+            be = SV.GpuBackend(local, lam=args.lam or 8.0)
             srv = SV.Server(be, scenes, hbm_budget=int(args.hbm_gb * (1 << 30)))
             trace = S.poisson_trace(args.requests, rate, len(scenes), seed=0)
             res = replay(srv, SV, trace, scenes, prec)
@@ -390,7 +390,7 @@ def run_serve(args):
         paper = [S.paper_scene(0)]
         steady = {}
         for label, rate, n in (("30fps", 30.0, 90), ("unthrottled", 1e6, 240)):
-            be = SV.GpuBackend(local, lam=4.0)
+            be = SV.GpuBackend(local, lam=args.lam or 8.0)
             srv = SV.Server(be, paper, hbm_budget=int(args.hbm_gb * (1 << 30)), wave_rays=24e6, band_rows=1137)
             trace = [dict(id=k, arrival_s=k / rate, scene=0, width=965, height=1137, spp=16, angle_deg=0.0)
                      for k in range(n)]

@@ -208,7 +208,7 @@ class GpuBackend:
     """Backend over the C ABI: resident scenes/grids, device outputs, one
     batched launch per wave on the server's own stream."""
 
-    def __init__(self, device: int = 0, lights=None, lam: float = 2.0, tuning: Optional[dict] = None):
+    def __init__(self, device: int = 0, lights=None, lam: float = 8.0, tuning: Optional[dict] = None):
         import torch
 
         from . import gbrt as G
