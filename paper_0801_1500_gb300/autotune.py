@@ -22,7 +22,7 @@ import numpy as np
 
 from . import gbrt as G
 
-LAMBDAS = (1.0, 2.0, 4.0, 8.0)
+LAMBDAS = (1.0, 2.0, 4.0, 8.0, 16.0)
 REFILLS = (8, 12, 16, 20, 24)
 TILES = ((8, 4), (16, 2), (4, 8), (32, 1))
 BLOCKS = (128, 256)
