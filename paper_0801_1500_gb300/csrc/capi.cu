@@ -497,6 +497,7 @@ GBRT_API int gbrt_ao_probe(gbrt_ctx* ctx, const gbrt_scene* scene, const gbrt_gr
         int rc = grid_refresh_host(const_cast<gbrt_grid*>(grid));
         if (rc != GBRT_OK) return rc;
     }
+    if (grid->dev.cells == nullptr) return GBRT_EINVAL;  // a grid left unusable by a failed rebuild
     FrameDev f = make_frame(scene, grid, &cam, 1, 1, ao_samples, &lights, params, nullptr, nullptr, nullptr);
     return launch_ao_probe(ctx, f, pts, nrm, n, out_visibility);
 }
