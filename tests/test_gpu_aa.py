@@ -96,7 +96,7 @@ def test_supersampled_pinhole_paper_scene_sampled(G, R, oracle, paper):
     cam = S.pinhole_camera(paper, W, H, 30.0, aa=m)
     lights = S.default_lights()
     p = S.Params(ao_samples=16, seed=0)
-    scene, grid = R.upload(paper, lam=2.0)
+    scene, grid = R.upload(paper, lam=8.0)
     rgb, ids, vis = render_aa(G, R, scene, grid, cam, W, H, lights, p)
     rng = np.random.default_rng(11)
     pixels = np.sort(rng.choice(W * H, 3000, replace=False))

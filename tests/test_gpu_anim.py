@@ -146,7 +146,7 @@ def test_paper_scene_md_frame_vs_oracle(G, R, oracle):
     W, H = 965, 1137
     lights = S.default_lights()
     p = S.Params(ao_samples=16, seed=0, frame=12)
-    scene, grid = R.upload(base, lam=2.0)
+    scene, grid = R.upload(base, lam=8.0)
     for k in range(1, 13):
         fr = traj.frame(k)
         G.gbrt_scene_update(R.ctx, scene, fr.spheres, fr.cylinders)
