@@ -628,7 +628,7 @@ def main():
         shadowed = S.paper_1mp(scene=w.scene)
         shadowed.params.shadows = True
         pin_aa = S.Workload("paper_26318obj_965x1137_pinhole_aa2x2_spp16", w.scene, W, H, S.Params(ao_samples=16),
-                            w.lights, S.pinhole_camera(w.scene, W, H, 30.0, aa=2))
+                            w.lights, S.pinhole_camera(w.scene, W, H, fov_deg=30.0, aa=2))
         side = (("fp64_path_1.1MP", S.paper_1mp(precision=other, scene=w.scene), 3),
                 ("fp32_path_1.1MP_direct_light_shadows", shadowed, 5),
                 ("fp32_path_1.1MP_pinhole_2x2_supersampled", pin_aa, 3),

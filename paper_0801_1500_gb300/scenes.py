@@ -233,12 +233,13 @@ def pinhole_camera(scene: Scene, width: int, height: int, angle_deg: float = 0.0
     """Pinhole view of the scene down -z, rotated by ``angle_deg`` about +y.
 
     The vertical field of view is ``fov_deg``; the eye sits on the view axis
-    through the box centre, far enough that the box's bounding sphere (times
-    ``margin``) fits the vertical field. ``aa`` is the sub-pixel grid side.
+    through the box centre, far enough that a ball of the box's largest half
+    extent (times ``margin``) -- the globule -- fits the vertical field. ``aa``
+    is the sub-pixel grid side.
     """
     lo, hi = scene.bounds()
     ctr = 0.5 * (lo + hi)
-    rad = max(0.5 * float(np.linalg.norm(hi - lo)), 1e-6) * margin
+    rad = max(0.5 * float(np.max(hi - lo)), 1e-6) * margin
     hh = math.tan(math.radians(fov_deg) / 2.0)
     hw = hh * width / float(height)
     dist = rad / math.sin(math.radians(fov_deg) / 2.0)

@@ -77,7 +77,7 @@ def check(rgb, ids, vis, ref, W, m, pixels, where):
 def test_supersampled_small_frame(G, R, oracle, prec, m, kind):
     sc = S.globule(2000, 1900, 25.0, seed=0)
     W, H = 97, 61   # ragged against the 8 x 4 primary tiles at every m
-    cam = S.ortho_camera(sc, W, H, angle_deg=15.0) if kind == "ortho" else S.pinhole_camera(sc, W, H, 40.0)
+    cam = S.ortho_camera(sc, W, H, angle_deg=15.0) if kind == "ortho" else S.pinhole_camera(sc, W, H, angle_deg=40.0)
     cam = with_aa(cam, m)
     lights = S.default_lights()
     p = S.Params(ao_samples=6, seed=4, frame=2, precision=prec)
@@ -93,7 +93,7 @@ def test_supersampled_small_frame(G, R, oracle, prec, m, kind):
 def test_supersampled_pinhole_paper_scene_sampled(G, R, oracle, paper):
     # 26,318 objects, 965 x 1137 pinhole view, 2 x 2 sub-samples, 16 AO samples, FP32 path
     W, H, m = 965, 1137, 2
-    cam = S.pinhole_camera(paper, W, H, 30.0, aa=m)
+    cam = S.pinhole_camera(paper, W, H, fov_deg=30.0, aa=m)
     lights = S.default_lights()
     p = S.Params(ao_samples=16, seed=0)
     scene, grid = R.upload(paper, lam=8.0)

@@ -335,3 +335,21 @@ def test_direct_light_shadows_paper_scene(G, R, oracle, paper):
     st = compare(rgb, ids, vis, ref)
     print("paper 1.1MP shadows", st)
     assert_parity(st, "shadows paper")
+
+
+@pytest.mark.parametrize("lam", [2.0, 8.0])
+def test_largest_serving_scene(G, R, oracle, lam):
+    # the 250k-object scene of the serving trace (the largest grid: up to
+    # 2M cells at lambda 8), pinhole view from outside, FP32 path vs the oracle
+    sc = S.globule(127500, 121125, 60.0 * (127500 / 13500.0) ** (1.0 / 3.0), seed=1)
+    W, H = 192, 160
+    cam = S.pinhole_camera(sc, W, H, angle_deg=25.0, fov_deg=35.0)
+    p = S.Params(ao_samples=4, seed=7)
+    scene, grid = R.upload(sc, lam=lam)
+    rgb, ids, vis = gpu_frame(G, R, scene, grid, cam, W, H, S.default_lights(), p)
+    ref = oracle.render(sc, cam, W, H, S.default_lights(), p, mode="grid", lam=2.0)
+    st = compare(rgb, ids, vis, ref)
+    assert_parity(st, f"250k objects lambda {lam}")
+    assert st["vis_eq"] >= 0.999
+    assert 0.3 < (ref["id"] != 0xFFFFFFFF).mean() < 0.95
+    R.free(scene, grid)
