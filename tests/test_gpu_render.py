@@ -92,6 +92,23 @@ def test_ragged_frames(G, R, oracle, W, H, spp, prec):
     R.free(scene, grid)
 
 
+@pytest.mark.parametrize("W,H", [(65536, 1), (1, 65536)])
+def test_largest_width_and_height(G, R, oracle, W, H):
+    # the largest accepted width / height: one line of pixels across the scene
+    sc = S.globule(600, 570, 15.0, seed=7)
+    # square pixels, the line spanning the globule
+    half = 16.0
+    cam = S.Camera(eye=(0.0, 0.0, 40.0), dir=(0.0, 0.0, -1.0), up=(0.0, 1.0, 0.0), right=(1.0, 0.0, 0.0),
+                   half_w=half * min(1.0, W / H), half_h=half * min(1.0, H / W))
+    p = S.Params(ao_samples=2, seed=5)
+    scene, grid = R.upload(sc, lam=2.0)
+    rgb, ids, vis = gpu_frame(G, R, scene, grid, cam, W, H, S.default_lights(), p)
+    ref = oracle.render(sc, cam, W, H, S.default_lights(), p, mode="grid", lam=2.0)
+    assert 0.5 < (ref["id"] != 0xFFFFFFFF).mean() < 1.0
+    assert_parity(compare(rgb, ids, vis, ref), f"{W}x{H}")
+    R.free(scene, grid)
+
+
 @pytest.fixture(scope="module")
 def paper(G, R):
     w = S.paper_1mp()
@@ -206,7 +223,8 @@ def test_invalid_arguments_rejected(G, R):
     scene, grid = R.upload(sc)
     cam = S.ortho_camera(sc, 8, 8)
     out = torch.empty((8, 8, 3), device="cuda")
-    for W, H, spp in [(0, 8, 4), (8, -1, 4), (8, 8, -1), (8, 8, 100000)]:
+    for W, H, spp in [(0, 8, 4), (8, -1, 4), (8, 8, -1), (8, 8, 100000), (65537, 1, 4), (1, 65537, 4),
+                      (65536, 32768, 4)]:   # width, height <= 65536 and width * height < 2^31
         with pytest.raises(G.GbrtError) as e:
             G.gbrt_render(R.ctx, scene, grid, cam, W, H, spp, S.default_lights(), S.Params(), out)
         assert e.value.code == G.EINVAL
