@@ -633,7 +633,8 @@ def main():
                 ("fp32_path_1.1MP_direct_light_shadows", shadowed, 5),
                 ("fp32_path_1.1MP_pinhole_2x2_supersampled", pin_aa, 3),
                 ("fp32_path_4.4MP", mid, 3),
-                ("fp32_path_17.6MP", S.paper_17mp(precision=S.PRECISION_FP32, scene=w.scene), 3))
+                ("fp32_path_17.6MP", S.paper_17mp(precision=S.PRECISION_FP32, scene=w.scene), 3),
+                ("fp64_path_17.6MP", S.paper_17mp(precision=S.PRECISION_FP64, scene=w.scene), 1))
         for name, wk, nsteps in side:
             o2 = torch.empty((wk.height, wk.width, 3),
                              dtype=torch.float64 if wk.params.precision == S.PRECISION_FP64 else torch.float32,
