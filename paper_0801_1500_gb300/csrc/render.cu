@@ -1,14 +1,19 @@
 // Render kernels, wavefront style, for one frame or a batch of frames:
+//   k_patch_grids  (frames whose grid was rebuilt on the device) copies the
+//              rebuilt geometry into the frame descriptors;
 //   k_primary  persistent; each warp pulls a 32-pixel tile of some frame from
 //              an atomic queue, walks the primary rays (nearest hit), refines
-//              the winner in FP64 and appends the hit (AO origin, normal) to
-//              its frame's hit list;
+//              the winner in its object's frame and appends the hit (AO
+//              origin, normal) to its frame's hit list;
 //   k_ao_plan  prefix sums of hits and AO rays per frame;
-//   k_ao_walk  persistent; each lane holds one AO shadow ray; a warp refills
-//              its idle lanes together (ballot + popc compaction) once fewer
-//              than `refill` lanes still hold a ray, so warps stay full while
-//              walks of very different length finish;
-//   k_shade    one thread per hit: Phong + skylight with V = escaped / spp.
+//   k_ao_walk  persistent; each lane holds one AO (or direct-light shadow)
+//              ray; a warp refills its idle lanes together from its ray pool
+//              once fewer than `refill` lanes still hold a ray, walks all of
+//              them in lockstep (several cells per iteration), expands the
+//              (ray, object) pairs over the lanes and tests them in full
+//              batches;
+//   k_shade    one thread per hit: Phong + skylight with V = escaped / spp;
+//   k_resolve  (supersampled frames) box-filters the finer raster.
 // Plus the AO probe and the raw Philox kernel.
 #include <string.h>
 
