@@ -1,7 +1,10 @@
 // Scene upload (input arrays -> device records + FP64 copies + scene box) and
 // the uniform-grid build: count -> exclusive scan -> scatter -> per-cell sort.
 // The grid is the acceleration structure of the tracer; its build is the
-// paper's "Preprocess" phase (Table 5).
+// paper's preprocessing phase (Table 5). For animated scenes the geometry can
+// be replaced in place (scene_update) and the grid rebuilt on the device with
+// no host round trip (grid_rebuild: the geometry itself is computed by a
+// one-thread kernel from the device-side scene box).
 #include <math.h>
 #include <string.h>
 
