@@ -317,7 +317,7 @@ struct __align__(16) AoRay {
 
 // Per-warp shared state of the cooperative AO walk.
 //   ray[lane]      the lane's ray (origin, tmax, direction)
-//   delta, split   where each ray's pairs of the current iteration find their
+//   sd             where each ray's pairs of the current iteration find their
 //                  items (one range per cell taken)
 //   owner          the ray whose pairs start at a position of the current chunk
 //   mbox[lane]     direct-mapped ids this ray already tested (rows padded to
@@ -336,20 +336,26 @@ constexpr unsigned AO_MIN_PAIRS = 6;
 // AO rays a warp claims from the global queue at once (its local pool)
 constexpr unsigned AO_CLAIM = 64;
 
+// 5 KB a warp in the FP32 path: four resident CTAs of 8 warps fit the 164 KB
+// shared-memory configuration, leaving 92 KB of the SM's 256 KB to the L1
+// that caches the walk's cell, item and object loads (the next larger
+// configuration would halve it to 60 KB; measured 1.5% slower).
 template <class R>
 struct AoWarp {
     AoRay<R> ray[32];
-    // item index of pair p of ray r: p + delta[g][r] for the last cell g whose
-    // pairs start at or before p (split[g][r])
-    unsigned delta[AO_CELLS][32];
-    unsigned split[AO_CELLS][32];
+    // item index of pair p of ray r: p + sd[g][r].y for the last cell g whose
+    // pairs start at or before p (sd[g][r].x)
+    uint2 sd[AO_CELLS][32];
     uint32_t owner[32];  // ray whose pairs start at this position of the current chunk
     uint32_t mbox[32][AO_MBOX + 1];
     ObjPtr<R> obj[32];
     const uint32_t* items[32];
     uint2 q[64];  // queued pairs (ray lane, object id)
-    uint2 fifo[32][AO_CELLS];  // cells a ray has loaded but not yet taken, oldest first
+    // cells a ray has loaded but not yet taken, oldest first: an iteration takes
+    // at least one of its at most AO_CELLS cells, so AO_CELLS - 1 wait at most
+    uint2 fifo[32][AO_CELLS - 1];
 };
+static_assert(sizeof(AoWarp<float>) <= 5120, "the FP32 AO walk's per-warp state outgrew its 5 KB");
 
 // Test queued pairs [0, n) (1 <= n <= 32), one per lane (lanes past n redo
 // pair 0 and discard it, so the batch runs without branches); returns the
@@ -496,7 +502,7 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
         for (int g = 0; g < AO_CELLS; ++g) {
             uint2 cr = make_uint2(0u, 0u);
             if (has) {
-                if ((unsigned)g < nf) {
+                if (g < AO_CELLS - 1 && (unsigned)g < nf) {
                     cr = S.fifo[lane][g];
                     ++avail;
                 } else if (!wend) {
@@ -557,8 +563,7 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
             unsigned run = ex;
 #pragma unroll
             for (int g = 0; g < AO_CELLS; ++g) {
-                S.delta[g][lane] = kg[g] - run;
-                S.split[g][lane] = run;
+                S.sd[g][lane] = make_uint2(run, kg[g] - run);
                 run += ng[g];
             }
             // 4. map pairs to (ray, object), drop the own object and re-tests,
@@ -574,10 +579,12 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
                 __syncwarp();
                 const unsigned p = base + lane < T ? base + lane : T - 1u;
                 const unsigned r = S.owner[31 - __clz(starts & (0xFFFFFFFFu >> (31 - lane)))];
-                unsigned di = S.delta[0][r];
+                unsigned di = S.sd[0][r].y;
 #pragma unroll
-                for (int g = 1; g < AO_CELLS; ++g)
-                    if (p >= S.split[g][r]) di = S.delta[g][r];
+                for (int g = 1; g < AO_CELLS; ++g) {
+                    const uint2 e = S.sd[g][r];
+                    if (p >= e.x) di = e.y;
+                }
                 const uint32_t id = __ldg(S.items[r] + (p + di));
                 uint32_t* slot = &S.mbox[r][id & (AO_MBOX - 1)];
                 const uint32_t seen = *slot;
