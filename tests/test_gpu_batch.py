@@ -107,3 +107,45 @@ def test_bands_equal_whole_frame(G):
             G.gbrt_sync(r.ctx)
             for x, y in zip(ref, o):
                 assert torch.equal(x, y)
+
+
+def test_orbit64_graph_batch_sampled_vs_oracle(G, oracle):
+    # the 64-frame orbit of the 26,318-object scene (512x512, 965x1137 and 1920x1080
+    # frames, 8-32 AO samples, seed = frame index) as one graph-replayed batch, the
+    # launch bench.py times; sampled pixels of frames of every size against the oracle
+    import torch
+    from gpu_common import assert_parity, compare
+    w = S.paper_1mp()
+    frames = S.orbit_frames(w.scene, 64)
+    with G.Renderer(0) as r:
+        scene, grid = r.upload(w.scene, lam=8.0)
+        items, outs = [], []
+        for f in frames:
+            p = S.Params(ao_samples=f["spp"], seed=f["seed"], frame=f["frame"])
+            o = (torch.full((f["height"], f["width"], 3), -1.0, device="cuda"),
+                 torch.full((f["height"], f["width"]), -7, dtype=torch.int32, device="cuda"),
+                 torch.full((f["height"], f["width"]), -7, dtype=torch.int32, device="cuda"))
+            outs.append(o)
+            items.append(G.make_item(scene, grid, f["camera"], f["width"], f["height"], f["spp"], w.lights, p, *o))
+        for _ in range(2):  # capture, then replay
+            G.gbrt_render_batch(r.ctx, items, G.BATCH_GRAPH)
+            G.gbrt_sync(r.ctx)
+        picked = {}
+        for k, f in enumerate(frames):
+            picked.setdefault((f["width"], f["height"]), []).append(k)
+        assert len(picked) == 3
+        rng = np.random.default_rng(64)
+        for size, ks in sorted(picked.items()):
+            for k in (ks[0], ks[-1]):
+                f = frames[k]
+                W, H = f["width"], f["height"]
+                p = S.Params(ao_samples=f["spp"], seed=f["seed"], frame=f["frame"])
+                pix = np.sort(rng.choice(W * H, 1500, replace=False))
+                ref = oracle.render(w.scene, f["camera"], W, H, w.lights, p, pixels=pix, mode="grid", lam=2.0)
+                rgb = outs[k][0].cpu().numpy().reshape(-1, 3).astype(np.float64)
+                ids = outs[k][1].cpu().numpy().view(np.uint32).ravel()
+                vis = outs[k][2].cpu().numpy().view(np.uint32).ravel()
+                st = compare(rgb, ids, vis, ref, pixels=pix)
+                assert_parity(st, f"orbit frame {k} {W}x{H} spp {f['spp']}")
+                assert st["vis_eq"] >= 0.995, (k, st)
+        r.free(scene, grid)
