@@ -339,7 +339,7 @@ constexpr unsigned AO_CLAIM = 64;
 // 5 KB a warp in the FP32 path: four resident CTAs of 8 warps fit the 164 KB
 // shared-memory configuration, leaving 92 KB of the SM's 256 KB to the L1
 // that caches the walk's cell, item and object loads (the next larger
-// configuration would halve it to 60 KB; measured 1.5% slower).
+// configuration would leave it 60 KB; measured 1.5% slower).
 template <class R>
 struct AoWarp {
     AoRay<R> ray[32];
@@ -372,10 +372,11 @@ __device__ __forceinline__ unsigned ao_test_batch(AoWarp<R>& S, int lane, unsign
     return __reduce_or_sync(FULL, hit ? (1u << r) : 0u);
 }
 
-// Lockstep cooperative walk: every iteration each active ray advances one cell
-// (all lanes run the same step code); the warp lays the (ray, item) pairs of
-// those cells out densely with a scan, drops the ray's own object and
-// re-tests, compacts the survivors and tests them in full batches of 32.
+// Lockstep cooperative walk: every iteration each active ray takes its next
+// one to AO_CELLS cells (all lanes run the same step code); the warp lays the
+// (ray, item) pairs of those cells out densely with a scan, drops the ray's
+// own object and re-tests, compacts the survivors and tests them in full
+// batches of 32.
 template <class R>
 __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDev b) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
