@@ -546,24 +546,41 @@ def main():
         G.gbrt_sync(r.ctx)
         # (a) a stream of frames: each step enqueues its geometry copy, rebuild,
         #     render and image copy-back (asynchronous host outputs); the host
-        #     waits once, after the last step
+        #     waits once, after the last step. Frames alternate between two
+        #     contexts (each its own CUDA stream, scene and grid), so one
+        #     frame's geometry update and grid rebuild overlap the other's
+        #     render; "one_context" is the same stream of frames on one context.
         pa_async = G.make_params(p, out_flags=G.HOST_PTRS | G.HOST_ASYNC)
         outs_async = [torch.empty(out.shape, dtype=out.dtype).pin_memory().numpy() for _ in range(2)]
+        r_b = G.Renderer(local, torch.cuda.Stream(dev))
+        sc_b = G.gbrt_scene_upload(r_b.ctx, pinned["s"], pinned["c"], pinned["i"], pinned["p"], G.HOST_PTRS)
+        gr_b = G.gbrt_grid_build(r_b.ctx, sc_b, lam)
+        G.gbrt_grid_rebuild(r_b.ctx, gr_b, sc_b)
+        G.gbrt_sync(r_b.ctx)
 
-        def stream_steps(n):
+        def stream_steps(n, lanes):
             for k in range(n):
-                G.gbrt_scene_update(r.ctx, sc2, pinned["s"], pinned["c"], G.HOST_PTRS)
-                G.gbrt_grid_rebuild(r.ctx, gr2, sc2)
-                G.gbrt_render(r.ctx, sc2, gr2, cam, W, H, spp, li, pa_async, outs_async[k % 2])
-            G.gbrt_sync(r.ctx)
+                c, sc_k, gr_k = lanes[k % len(lanes)]
+                G.gbrt_scene_update(c, sc_k, pinned["s"], pinned["c"], G.HOST_PTRS)
+                G.gbrt_grid_rebuild(c, gr_k, sc_k)
+                G.gbrt_render(c, sc_k, gr_k, cam, W, H, spp, li, pa_async, outs_async[k % 2])
+            for c, _, _ in lanes:
+                G.gbrt_sync(c)
 
-        stream_steps(3)
+        two = [(r.ctx, sc2, gr2), (r_b.ctx, sc_b, gr_b)]
         n_stream = max(10, args.steps)
-        torch.cuda.synchronize(dev)
-        t1 = time.perf_counter()
-        stream_steps(n_stream)
-        t_stream = (time.perf_counter() - t1) / n_stream
-        assert np.array_equal(outs_async[0], outs_async[1])  # the same frame, copied back each step
+        t_lanes = {}
+        for name, lanes in (("two", two), ("one", two[:1])):
+            stream_steps(3, lanes)
+            torch.cuda.synchronize(dev)
+            t1 = time.perf_counter()
+            stream_steps(n_stream, lanes)
+            t_lanes[name] = (time.perf_counter() - t1) / n_stream
+            assert np.array_equal(outs_async[0], outs_async[1])  # the same frame, copied back each step
+        t_stream = t_lanes["two"]
+        G.gbrt_grid_free(r_b.ctx, gr_b)
+        G.gbrt_scene_free(r_b.ctx, sc_b)
+        r_b.close()
         # (b) one frame at a time: the host waits for every image
         tt = []
         for k in range(n_e2e + 2):
@@ -595,7 +612,10 @@ def main():
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(host_out.nbytes),
                "ms_per_step": round(1e3 * t_stream, 3), "fps": round(1.0 / t_stream, 2),
                "path": "scene_update + grid_rebuild + render with asynchronous host image, per step; "
-                       f"{n_stream} steps, one wait at the end",
+                       f"{n_stream} steps alternating between two contexts, one wait at the end",
+               "one_context": {"ms_per_step": round(1e3 * t_lanes["one"], 3),
+                               "Mrays_s": round(rays_per_step / t_lanes["one"] / 1e6, 3),
+                               "path": "the same stream of frames on one context"},
                "per_frame_wait": {"ms_per_step": round(1e3 * sum(tt) / len(tt), 3),
                                   "Mrays_s": round(rays_per_step / (sum(tt) / len(tt)) / 1e6, 3),
                                   "path": "the same calls, the host waiting for each image"},

@@ -132,10 +132,14 @@ typedef struct gbrt_lights {
  *              (the call then synchronises). GBRT_HOST_PTRS | GBRT_HOST_ASYNC:
  *              host outputs too, but the call returns once the copies are
  *              enqueued; the outputs are complete, and device-side errors
- *              reported, at the next gbrt_sync. Page-locked host memory makes
- *              the copies truly asynchronous; successive calls are ordered on
- *              the context's stream, so a stream of frames runs without a
- *              host round trip per frame. */
+ *              reported, at the next gbrt_sync (a synchronisation of the
+ *              caller's stream alone does not cover the copies). The render
+ *              goes into one of two device staging buffers of the context,
+ *              used in turn, and the copies run on a stream of the context's
+ *              own once its kernels are done, so one frame's copy overlaps the
+ *              next frame's work; page-locked host memory makes them truly
+ *              asynchronous. A stream of frames thus runs without a host round
+ *              trip per frame. */
 typedef struct gbrt_params {
     int32_t precision;
     int32_t out_flags;

@@ -153,16 +153,31 @@ int err_of(cudaError_t e) {
     return e == cudaErrorMemoryAllocation ? GBRT_ENOMEM : GBRT_EDEVICE;
 }
 
-int ensure_out(Ctx* c, size_t bytes) {
-    if (c->d_out_bytes >= bytes) return GBRT_OK;
-    if (c->d_out) {
-        cudaStreamSynchronize(c->stream);
-        cudaFree(c->d_out);
-        c->d_out = nullptr;
-        c->d_out_bytes = 0;
+// Staging buffer `slot` of host-output renders, at least `bytes` long; the
+// copy stream and its events are created on first use.
+int ensure_out(Ctx* c, int slot, size_t bytes) {
+    if (!c->copy_stream) {
+        if (cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
+            c->copy_stream = nullptr;
+            return GBRT_EDEVICE;
+        }
     }
-    int rc = err_of(cudaMalloc(&c->d_out, bytes));
-    if (rc == GBRT_OK) c->d_out_bytes = bytes;
+    for (int k = 0; k < 2; ++k) {
+        if ((!c->out_ready[k] && cudaEventCreateWithFlags(&c->out_ready[k], cudaEventDisableTiming) != cudaSuccess) ||
+            (!c->out_free[k] && cudaEventCreateWithFlags(&c->out_free[k], cudaEventDisableTiming) != cudaSuccess))
+            return GBRT_EDEVICE;
+    }
+    if (c->d_out_bytes[slot] >= bytes) return GBRT_OK;
+    if (c->d_out[slot]) {
+        // a render or a copy in flight may still use it
+        cudaStreamSynchronize(c->stream);
+        cudaStreamSynchronize(c->copy_stream);
+        cudaFree(c->d_out[slot]);
+        c->d_out[slot] = nullptr;
+        c->d_out_bytes[slot] = 0;
+    }
+    int rc = err_of(cudaMalloc(&c->d_out[slot], bytes));
+    if (rc == GBRT_OK) c->d_out_bytes[slot] = bytes;
     return rc;
 }
 
@@ -180,6 +195,15 @@ int read_error_word(Ctx* c) {
     if (w & ERR_GRID_CAPACITY) return GBRT_ECAPACITY;
     if (w) return GBRT_EINVAL;
     return GBRT_OK;
+}
+
+// Wait for the host-output copies, then read the error word.
+int sync_all(Ctx* c) {
+    if (c->copy_stream && cudaStreamSynchronize(c->copy_stream) != cudaSuccess) {
+        read_error_word(c);
+        return GBRT_EDEVICE;
+    }
+    return read_error_word(c);
 }
 
 }  // namespace
@@ -246,6 +270,7 @@ GBRT_API int gbrt_set_stream(gbrt_ctx* ctx, void* cuda_stream) {
     DeviceGuard g(ctx->device);
     // work already enqueued reads the context's buffers: drain the old stream
     cudaStreamSynchronize(ctx->stream);
+    if (ctx->copy_stream) cudaStreamSynchronize(ctx->copy_stream);
     ctx->stream = (cudaStream_t)cuda_stream;
     return GBRT_OK;
 }
@@ -253,13 +278,22 @@ GBRT_API int gbrt_set_stream(gbrt_ctx* ctx, void* cuda_stream) {
 GBRT_API int gbrt_sync(gbrt_ctx* ctx) {
     if (!ctx) return GBRT_EINVAL;
     DeviceGuard g(ctx->device);
-    return read_error_word(ctx);
+    return sync_all(ctx);
 }
 
 GBRT_API int gbrt_destroy(gbrt_ctx* ctx) {
     if (!ctx) return GBRT_OK;
     DeviceGuard g(ctx->device);
     cudaStreamSynchronize(ctx->stream);
+    if (ctx->copy_stream) {
+        cudaStreamSynchronize(ctx->copy_stream);
+        cudaStreamDestroy(ctx->copy_stream);
+    }
+    for (int k = 0; k < 2; ++k) {
+        if (ctx->out_ready[k]) cudaEventDestroy(ctx->out_ready[k]);
+        if (ctx->out_free[k]) cudaEventDestroy(ctx->out_free[k]);
+        cudaFree(ctx->d_out[k]);
+    }
     if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
     if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
     for (int k = 0; k < 5; ++k)
@@ -267,7 +301,6 @@ GBRT_API int gbrt_destroy(gbrt_ctx* ctx) {
     cudaEventDestroy(ctx->staging_done);
     cudaFree(ctx->d_err);
     cudaFreeHost(ctx->h_err);
-    cudaFree(ctx->d_out);
     cudaFree(ctx->d_hits);
     cudaFree(ctx->d_vis);
     cudaFree(ctx->d_lmask);
@@ -413,11 +446,16 @@ GBRT_API int gbrt_render(gbrt_ctx* ctx, const gbrt_scene* scene, const gbrt_grid
     void* d_rgb = out_rgb;
     uint32_t* d_ids = out_hit_ids;
     uint32_t* d_vis = out_ao_visible;
+    const int slot = ctx->out_slot;
     if (host) {
         size_t need = rgb_bytes + (out_hit_ids ? npx * 4 : 0) + (out_ao_visible ? npx * 4 : 0);
-        rc = ensure_out(ctx, (need + 255) & ~(size_t)255);
+        rc = ensure_out(ctx, slot, (need + 255) & ~(size_t)255);
         if (rc != GBRT_OK) return rc;
-        char* base = (char*)ctx->d_out;
+        // the copy out of this buffer two renders ago must end before the
+        // render writes it
+        if (ctx->out_used[slot] && cudaStreamWaitEvent(ctx->stream, ctx->out_free[slot], 0) != cudaSuccess)
+            return GBRT_EDEVICE;
+        char* base = (char*)ctx->d_out[slot];
         d_rgb = base;
         size_t off = (rgb_bytes + 15) & ~(size_t)15;
         if (out_hit_ids) {
@@ -430,13 +468,21 @@ GBRT_API int gbrt_render(gbrt_ctx* ctx, const gbrt_scene* scene, const gbrt_grid
     rc = render_frames(ctx, &f, 1, false);
     if (rc != GBRT_OK) return rc;
     if (host) {
-        cudaError_t e = cudaMemcpyAsync(out_rgb, d_rgb, rgb_bytes, cudaMemcpyDeviceToHost, ctx->stream);
+        // the copies run on the copy stream once the render's kernels are done,
+        // overlapping whatever the context's stream does next
+        cudaStream_t cs = ctx->copy_stream;
+        cudaError_t e = cudaEventRecord(ctx->out_ready[slot], ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ctx->out_ready[slot], 0);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(out_rgb, d_rgb, rgb_bytes, cudaMemcpyDeviceToHost, cs);
         if (e == cudaSuccess && out_hit_ids)
-            e = cudaMemcpyAsync(out_hit_ids, d_ids, npx * 4, cudaMemcpyDeviceToHost, ctx->stream);
+            e = cudaMemcpyAsync(out_hit_ids, d_ids, npx * 4, cudaMemcpyDeviceToHost, cs);
         if (e == cudaSuccess && out_ao_visible)
-            e = cudaMemcpyAsync(out_ao_visible, d_vis, npx * 4, cudaMemcpyDeviceToHost, ctx->stream);
+            e = cudaMemcpyAsync(out_ao_visible, d_vis, npx * 4, cudaMemcpyDeviceToHost, cs);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->out_free[slot], cs);
         if (e != cudaSuccess) return err_of(e);
-        return async ? GBRT_OK : read_error_word(ctx);
+        ctx->out_used[slot] = true;
+        ctx->out_slot = slot ^ 1;
+        return async ? GBRT_OK : sync_all(ctx);
     }
     return GBRT_OK;
 }

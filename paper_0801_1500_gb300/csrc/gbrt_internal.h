@@ -19,9 +19,16 @@ struct Ctx {
     uint32_t* h_err = nullptr;   // pinned mirror
     int64_t launches = 0;
     gbrt_tuning tuning{};
-    // device buffers for renders whose outputs are host memory
-    void* d_out = nullptr;
-    size_t d_out_bytes = 0;
+    // renders whose outputs are host memory: two device staging buffers used
+    // in turn, copied back on copy_stream, so one frame's copy overlaps the
+    // next frame's kernels
+    void* d_out[2] = {nullptr, nullptr};
+    size_t d_out_bytes[2] = {0, 0};
+    int out_slot = 0;                               // the buffer the next render uses
+    cudaStream_t copy_stream = nullptr;             // created at the first host-output render
+    cudaEvent_t out_ready[2] = {nullptr, nullptr};  // the render into buffer k finished
+    cudaEvent_t out_free[2] = {nullptr, nullptr};   // the copy out of buffer k finished
+    bool out_used[2] = {false, false};              // out_free[k] has been recorded
     // wavefront buffers: hit records, escaped-sample counts, descriptors, counters
     void* d_hits = nullptr;
     size_t hits_cap = 0;

@@ -271,6 +271,28 @@ def test_asynchronous_host_outputs(G, R):
                       ref_rgb, ref_ids)
         assert np.array_equal(rgb, ref_rgb) and np.array_equal(ids, ref_ids)
     assert not np.array_equal(outs[0][0], outs[1][0])  # different seeds, different AO
+    # a longer stream of frames of changing sizes (the two staging buffers
+    # alternate and grow mid-stream) with all three outputs, against renders
+    # into device memory
+    sizes = [(70, 50), (90, 64), (70, 50), (128, 80), (33, 17), (128, 80), (90, 64)]
+    outs = []
+    for k, (w, h) in enumerate(sizes):
+        p = S.Params(ao_samples=5, seed=10 + k, frame=k)
+        o = (torch.empty((h, w, 3), dtype=torch.float32).pin_memory().numpy(),
+             torch.empty((h, w), dtype=torch.int32).pin_memory().numpy().view(np.uint32),
+             torch.empty((h, w), dtype=torch.int32).pin_memory().numpy().view(np.uint32))
+        outs.append(o)
+        G.gbrt_render(R.ctx, scene, grid, S.ortho_camera(sc, w, h, angle_deg=15.0 * k), w, h, 5,
+                      S.default_lights(), G.make_params(p, out_flags=G.HOST_PTRS | G.HOST_ASYNC), *o)
+    G.gbrt_sync(R.ctx)
+    for k, ((w, h), o) in enumerate(zip(sizes, outs)):
+        p = S.Params(ao_samples=5, seed=10 + k, frame=k)
+        ref = R.render(scene, grid, S.ortho_camera(sc, w, h, angle_deg=15.0 * k), w, h, S.default_lights(), p,
+                       ids=True, vis=True)
+        G.gbrt_sync(R.ctx)
+        assert np.array_equal(o[0], ref[0].cpu().numpy()), k
+        assert np.array_equal(o[1], ref[1].cpu().numpy().view(np.uint32)), k
+        assert np.array_equal(o[2], ref[2].cpu().numpy().view(np.uint32)), k
     with pytest.raises(G.GbrtError):  # asynchronous outputs must be host outputs
         G.gbrt_render(R.ctx, scene, grid, cam, W, H, 6, S.default_lights(),
                       G.make_params(frames[0], out_flags=G.HOST_ASYNC), torch.empty((H, W, 3), device="cuda"))
