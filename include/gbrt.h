@@ -304,8 +304,11 @@ GBRT_API int gbrt_grid_rebuild(gbrt_ctx* ctx, gbrt_grid* grid, const gbrt_scene*
  * library keeps the finer raster's colours in a context buffer
  * (m^2 width height x 3 values) that it box-filters into out_rgb.
  * Output pointers are device memory unless params->out_flags has
- * GBRT_HOST_PTRS, in which case the library renders into its own device
- * buffer, copies back and synchronises. Asynchronous otherwise. */
+ * GBRT_HOST_PTRS, in which case the library renders into one of its two
+ * device staging buffers and copies back (then synchronises unless
+ * GBRT_HOST_ASYNC is set). Asynchronous otherwise. The grid must have been
+ * built for this scene (same object count) and both must live on the
+ * context's device: GBRT_EINVAL otherwise, before any work is enqueued. */
 GBRT_API int gbrt_render(gbrt_ctx* ctx, const gbrt_scene* scene, const gbrt_grid* grid, const gbrt_camera* camera,
                          int32_t width, int32_t height, int32_t ao_samples, const gbrt_lights* lights,
                          const gbrt_params* params, void* out_rgb, uint32_t* out_hit_ids,

@@ -43,6 +43,8 @@ int check_frame_args(const gbrt_scene* scene, const gbrt_grid* grid, const gbrt_
         !std::isfinite(params->phong_exp) || !finite3(params->background))
         return GBRT_EINVAL;
     if (grid->dev.cells == nullptr) return GBRT_EINVAL;
+    // a grid lists ids of the scene it was built for, on that scene's device
+    if (grid->N != scene->S + scene->C || grid->device != scene->device) return GBRT_EINVAL;
     return GBRT_OK;
 }
 
@@ -359,6 +361,7 @@ GBRT_API int gbrt_grid_build(gbrt_ctx* ctx, const gbrt_scene* scene, float lambd
     if (!ctx || !scene || !out) return GBRT_EINVAL;
     *out = nullptr;
     if (!std::isfinite(lambda) || lambda > 1.0e6f) return GBRT_EINVAL;
+    if (scene->device != ctx->device) return GBRT_EINVAL;
     DeviceGuard g(ctx->device);
     if (!g.ok) return GBRT_EDEVICE;
     gbrt_grid* gr = new (std::nothrow) gbrt_grid();
@@ -433,6 +436,7 @@ GBRT_API int gbrt_render(gbrt_ctx* ctx, const gbrt_scene* scene, const gbrt_grid
     if (!ctx) return GBRT_EINVAL;
     int rc = check_frame_args(scene, grid, camera, width, height, ao_samples, lights, params, out_rgb);
     if (rc != GBRT_OK) return rc;
+    if (scene->device != ctx->device) return GBRT_EINVAL;
     if (params->out_flags & ~(GBRT_HOST_PTRS | GBRT_HOST_ASYNC)) return GBRT_EINVAL;
     if ((params->out_flags & GBRT_HOST_ASYNC) && !(params->out_flags & GBRT_HOST_PTRS)) return GBRT_EINVAL;
     DeviceGuard g(ctx->device);
@@ -495,6 +499,7 @@ GBRT_API int gbrt_render_batch(gbrt_ctx* ctx, const gbrt_render_item* items, int
         int rc = check_frame_args(it.scene, it.grid, &it.camera, it.width, it.height, it.ao_samples, &it.lights,
                                   &it.params, it.out_rgb);
         if (rc != GBRT_OK) return rc;
+        if (it.scene->device != ctx->device) return GBRT_EINVAL;
         if (it.params.out_flags != 0) return GBRT_EINVAL;
         if (!(it.row_begin == 0 && it.row_end == 0) &&
             !(0 <= it.row_begin && it.row_begin < it.row_end && it.row_end <= it.height))
@@ -532,6 +537,8 @@ GBRT_API int gbrt_ao_probe(gbrt_ctx* ctx, const gbrt_scene* scene, const gbrt_gr
     if (ao_samples < 0 || ao_samples > GBRT_MAX_PROBE_SAMPLES) return GBRT_EINVAL;
     if (params->precision != GBRT_FP32 && params->precision != GBRT_FP64) return GBRT_EINVAL;
     if (!(params->eps >= 0) || !(params->ao_maxdist > 0)) return GBRT_EINVAL;
+    if (grid->N != scene->S + scene->C || grid->device != scene->device || scene->device != ctx->device)
+        return GBRT_EINVAL;
     DeviceGuard g(ctx->device);
     if (!g.ok) return GBRT_EDEVICE;
     gbrt_camera cam;

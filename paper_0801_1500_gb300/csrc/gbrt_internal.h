@@ -121,6 +121,7 @@ struct Grid {
     size_t bytes = 0;
     float lambda = 0.f;
     int64_t N = 0;  // objects of the scene it was built for
+    int device = 0;  // the scene's device
     // device-side rebuilds (gbrt_grid_rebuild): the authoritative geometry is
     // d_geom on the device; renders copy it into their frame descriptors
     bool dynamic = false;

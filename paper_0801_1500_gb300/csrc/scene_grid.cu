@@ -618,6 +618,7 @@ int grid_build(Ctx* ctx, const Scene* s, float lambda, Grid* g) {
     g->lambda = lambda;
     const int64_t N = s->S + s->C;
     g->N = N;
+    g->device = s->device;
     GridDev& d = g->dev;
     if (s->box_stale) {
         rc = scene_refresh_host(const_cast<Scene*>(s), ctx->stream);

@@ -228,7 +228,23 @@ def test_invalid_arguments_rejected(G, R):
         with pytest.raises(G.GbrtError) as e:
             G.gbrt_render(R.ctx, scene, grid, cam, W, H, spp, S.default_lights(), S.Params(), out)
         assert e.value.code == G.EINVAL
+    # a grid built for another scene (another object count) would list ids
+    # past this scene's arrays: rejected by render, batch and probe
+    other = S.globule(40, 35, 5.0, seed=3)
+    o_scene, o_grid = R.upload(other)
+    with pytest.raises(G.GbrtError) as e:
+        G.gbrt_render(R.ctx, scene, o_grid, cam, 8, 8, 4, S.default_lights(), S.Params(), out)
+    assert e.value.code == G.EINVAL
+    with pytest.raises(G.GbrtError) as e:
+        G.gbrt_render_batch(R.ctx, [G.make_item(o_scene, grid, cam, 8, 8, 4, S.default_lights(), S.Params(), out)])
+    assert e.value.code == G.EINVAL
+    pts = torch.zeros((1, 3), dtype=torch.float64, device="cuda")
+    vis = torch.empty(1, device="cuda")
+    with pytest.raises(G.GbrtError) as e:
+        G.gbrt_ao_probe(R.ctx, o_scene, grid, pts, pts, 4, S.Params(), vis)
+    assert e.value.code == G.EINVAL
     G.gbrt_sync(R.ctx)
+    R.free(o_scene, o_grid)
     R.free(scene, grid)
 
 
