@@ -10,8 +10,8 @@
 //              ray; a warp refills its idle lanes together from its ray pool
 //              once fewer than `refill` lanes still hold a ray, walks all of
 //              them in lockstep (several cells per iteration), expands the
-//              (ray, object) pairs over the lanes and tests them in full
-//              batches;
+//              (ray, object) pairs over the lanes and tests them 32 at a
+//              time;
 //   k_shade    one thread per hit: Phong + skylight with V = escaped / spp;
 //   k_resolve  (supersampled frames) box-filters the finer raster.
 // Plus the AO probe and the raw Philox kernel.
@@ -320,15 +320,15 @@ struct __align__(16) AoRay {
 //   sd             where each ray's pairs of the current iteration find their
 //                  items (one range per cell taken)
 //   owner          the ray whose pairs start at a position of the current chunk
-//   mbox[lane]     direct-mapped ids this ray already tested (rows padded to
-//                  AO_MBOX + 1 words so distinct rays and slots fall in
-//                  distinct banks); a re-test of a missed object cannot hit,
-//                  so skipping it is exact
+//   mbox[lane]     direct-mapped ids this ray already tested (rows padded by
+//                  one word so distinct rays and slots fall in distinct
+//                  banks); a re-test of a missed object cannot hit, so
+//                  skipping it is exact
 //   obj, items     the ray's scene records and grid item list (batches mix
 //                  scenes)
-//   q              surviving (ray, object) pairs waiting for a full test batch
 //   fifo[lane]     cells the ray has stepped to and loaded but not yet taken
-constexpr int AO_MBOX = 8;
+//   q              (FP64 path) surviving (ray, object) pairs waiting for a
+//                  full test batch
 // cells each active ray takes per lockstep iteration: further cells while it
 // holds fewer than AO_MIN_PAIRS candidates, at most AO_CELLS
 constexpr int AO_CELLS = 4;
@@ -336,30 +336,55 @@ constexpr unsigned AO_MIN_PAIRS = 6;
 // AO rays a warp claims from the global queue at once (its local pool)
 constexpr unsigned AO_CLAIM = 64;
 
-// 5 KB a warp in the FP32 path: four resident CTAs of 8 warps fit the 164 KB
-// shared-memory configuration, leaving 92 KB of the SM's 256 KB to the L1
-// that caches the walk's cell, item and object loads (the next larger
-// configuration would leave it 60 KB; measured 1.5% slower).
+// Per-precision choices. FP32: a 4-slot mailbox and pairs tested where they
+// were mapped, which keeps the walk's shared state at 4 KB a warp (below).
+// FP64: the test occupies the FP64 pipe, so lanes left idle cost more than
+// shared memory -- an 8-slot mailbox, and surviving pairs queued and tested
+// in full batches of 32 (in-place tests measured 13% slower there).
 template <class R>
-struct AoWarp {
+struct AoCfg;
+template <>
+struct AoCfg<float> {
+    static constexpr int mbox = 4;
+    static constexpr bool queue = false;
+};
+template <>
+struct AoCfg<double> {
+    static constexpr int mbox = 8;
+    static constexpr bool queue = true;
+};
+
+template <class R, bool Q = AoCfg<R>::queue>
+struct AoQueue {};
+template <class R>
+struct AoQueue<R, true> {
+    uint2 q[64];  // queued pairs (ray lane, object id)
+};
+
+// 4 KB a warp in the FP32 path: four resident CTAs of 8 warps fit the 132 KB
+// shared-memory configuration, leaving 124 KB of the SM's 256 KB to the L1
+// that caches the walk's cell, item and object loads. Measured: 5.25 KB a
+// warp (60 KB of L1) 2.5% slower, 5 KB (92 KB of L1, with an 8-slot mailbox
+// and a test queue) 1% slower.
+template <class R>
+struct AoWarp : AoQueue<R> {
     AoRay<R> ray[32];
     // item index of pair p of ray r: p + sd[g][r].y for the last cell g whose
     // pairs start at or before p (sd[g][r].x)
     uint2 sd[AO_CELLS][32];
     uint32_t owner[32];  // ray whose pairs start at this position of the current chunk
-    uint32_t mbox[32][AO_MBOX + 1];
+    uint32_t mbox[32][AoCfg<R>::mbox + 1];
     ObjPtr<R> obj[32];
     const uint32_t* items[32];
-    uint2 q[64];  // queued pairs (ray lane, object id)
     // cells a ray has loaded but not yet taken, oldest first: an iteration takes
     // at least one of its at most AO_CELLS cells, so AO_CELLS - 1 wait at most
     uint2 fifo[32][AO_CELLS - 1];
 };
-static_assert(sizeof(AoWarp<float>) <= 5120, "the FP32 AO walk's per-warp state outgrew its 5 KB");
+static_assert(sizeof(AoWarp<float>) <= 4096, "the FP32 AO walk's per-warp state outgrew its 4 KB");
 
-// Test queued pairs [0, n) (1 <= n <= 32), one per lane (lanes past n redo
-// pair 0 and discard it, so the batch runs without branches); returns the
-// rays hit, as bits.
+// FP64 path: test queued pairs [0, n) (1 <= n <= 32), one per lane (lanes
+// past n redo pair 0 and discard it, so the batch runs without branches);
+// returns the rays hit, as bits.
 template <class R>
 __device__ __forceinline__ unsigned ao_test_batch(AoWarp<R>& S, int lane, unsigned n) {
     const unsigned idx = (unsigned)lane < n ? (unsigned)lane : 0u;
@@ -374,9 +399,8 @@ __device__ __forceinline__ unsigned ao_test_batch(AoWarp<R>& S, int lane, unsign
 
 // Lockstep cooperative walk: every iteration each active ray takes its next
 // one to AO_CELLS cells (all lanes run the same step code); the warp lays the
-// (ray, item) pairs of those cells out densely with a scan, drops the ray's
-// own object and re-tests, compacts the survivors and tests them in full
-// batches of 32.
+// (ray, item) pairs of those cells out densely with a scan and tests them 32
+// at a time, one pair per lane, skipping the ray's own object and re-tests.
 template <class R>
 __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDev b) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -466,11 +490,11 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
                         S.obj[lane] = Obj<R>::base(F.scene);
                         S.items[lane] = F.grid.items;
 #pragma unroll
-                        for (int m = 0; m < AO_MBOX; ++m) S.mbox[lane][m] = GBRT_MISS;
+                        for (int m = 0; m < AoCfg<R>::mbox; ++m) S.mbox[lane][m] = GBRT_MISS;
                         // the own object starts in the mailbox: it is skipped like a
                         // re-test while it stays there (testing it is harmless too --
                         // behind a convex outer side the ray cannot meet it again)
-                        if (self != GBRT_MISS) S.mbox[lane][self & (AO_MBOX - 1)] = self;
+                        if (self != GBRT_MISS) S.mbox[lane][self & (AoCfg<R>::mbox - 1)] = self;
                         nf = 0;
                         wend = false;
                         has = true;
@@ -567,8 +591,11 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
                 S.sd[g][lane] = make_uint2(run, kg[g] - run);
                 run += ng[g];
             }
-            // 4. map pairs to (ray, object), drop the own object and re-tests,
-            //    queue the survivors; test whenever 32 are queued
+            // 4. map pairs to (ray, object) 32 at a time, skip the own object
+            //    and re-tests, and test the rest: in place in the FP32 path
+            //    (the skipped pairs' lanes compute and discard, so the test runs
+            //    without branches), through the queue in full batches of 32 in
+            //    the FP64 path
             unsigned qn = 0;
             for (unsigned base = 0; base < T; base += 32) {
                 // rays mark where their pairs start inside this chunk; a pair's
@@ -587,25 +614,36 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
                     if (p >= e.x) di = e.y;
                 }
                 const uint32_t id = __ldg(S.items[r] + (p + di));
-                uint32_t* slot = &S.mbox[r][id & (AO_MBOX - 1)];
+                uint32_t* slot = &S.mbox[r][id & (AoCfg<R>::mbox - 1)];
                 const uint32_t seen = *slot;
                 const bool keep = base + lane < T && seen != id;
-                const unsigned bal = __ballot_sync(FULL, keep);
-                if (keep) {
-                    *slot = id;
-                    S.q[qn + __popc(bal & lt)] = make_uint2(r, id);
-                }
-                qn += __popc(bal);
-                __syncwarp();
-                if (qn >= 32) {
-                    hitbits |= ao_test_batch(S, lane, 32u);
+                if constexpr (AoCfg<R>::queue) {
+                    const unsigned bal = __ballot_sync(FULL, keep);
+                    if (keep) {
+                        *slot = id;
+                        S.q[qn + __popc(bal & lt)] = make_uint2(r, id);
+                    }
+                    qn += __popc(bal);
                     __syncwarp();
-                    if ((unsigned)lane < qn - 32) S.q[lane] = S.q[32 + lane];
-                    qn -= 32;
+                    if (qn >= 32) {
+                        hitbits |= ao_test_batch(S, lane, 32u);
+                        __syncwarp();
+                        if ((unsigned)lane < qn - 32) S.q[lane] = S.q[32 + lane];
+                        qn -= 32;
+                        __syncwarp();
+                    }
+                } else {
+                    if (keep) *slot = id;
+                    const AoRay<R> ray = S.ray[r];
+                    R t;
+                    const bool hit = hit_object<R>(S.obj[r], id, ray.o, ray.d, R(0), ray.tmax, t) && keep;
+                    hitbits |= __reduce_or_sync(FULL, hit ? (1u << r) : 0u);
                     __syncwarp();
                 }
             }
-            if (qn > 0) hitbits |= ao_test_batch(S, lane, qn);
+            if constexpr (AoCfg<R>::queue) {
+                if (qn > 0) hitbits |= ao_test_batch(S, lane, qn);
+            }
         }
         // 5. any hit occludes the ray; a ray whose walk ended escapes
         if (has && ((hitbits >> lane) & 1u)) {
