@@ -129,6 +129,35 @@ def ptr(x):
     raise TypeError(f"cannot take the address of {type(x)}")
 
 
+def _buf(x, nbytes, host, where):
+    """Address of an argument buffer after checking that it is dense, in the
+    expected memory (host or device) and at least ``nbytes`` long; None passes
+    through and a raw integer address is taken as given. A mismatch raises
+    GbrtError(EINVAL) before the library is called."""
+    if x is None or isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous() or bool(x.is_cuda) == bool(host):
+            raise GbrtError(EINVAL, where)
+        size = x.numel() * x.element_size()
+    elif isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous or not host:
+            raise GbrtError(EINVAL, where)
+        size = x.nbytes
+    else:
+        raise TypeError(f"{where}: cannot take the address of {type(x)}")
+    if size < nbytes:
+        raise GbrtError(EINVAL, where)
+    return ptr(x)
+
+
+def _frame_bytes(camera, width, height, params):
+    """Bytes of a render's colour output and of each per-sub-sample output."""
+    m = max(1, int(camera.aa))
+    px = max(0, int(width)) * max(0, int(height))
+    return px * 3 * (8 if int(params.precision) == FP64 else 4), px * m * m * 4
+
+
 # ------------------------------------------------------------ struct builders
 
 def make_camera(cam) -> gbrt_camera:
@@ -201,14 +230,18 @@ def gbrt_scene_upload(ctx, spheres, cylinders, color_idx, palette, flags=None):
     """Arrays: torch CUDA tensors (device) or numpy arrays (host, flags = HOST_PTRS)."""
     if flags is None:
         flags = HOST_PTRS if isinstance(spheres, np.ndarray) else DEVICE_PTRS
-    if flags == HOST_PTRS:
+    host = flags == HOST_PTRS
+    if host:
         spheres = np.ascontiguousarray(spheres, np.float32)
         cylinders = np.ascontiguousarray(cylinders, np.float32)
         color_idx = np.ascontiguousarray(color_idx, np.uint32)
         palette = np.ascontiguousarray(palette, np.float32)
+    S, Cn, K = int(spheres.shape[0]), int(cylinders.shape[0]), int(palette.shape[0])
+    w = "gbrt_scene_upload"
     h = C.c_void_p()
-    rc = lib.gbrt_scene_upload(ctx, ptr(spheres), int(spheres.shape[0]), ptr(cylinders), int(cylinders.shape[0]),
-                               ptr(color_idx), ptr(palette), int(palette.shape[0]), int(flags), C.byref(h))
+    rc = lib.gbrt_scene_upload(ctx, _buf(spheres, 16 * S, host, w), S, _buf(cylinders, 28 * Cn, host, w), Cn,
+                               _buf(color_idx, 4 * (S + Cn), host, w), _buf(palette, 12 * K, host, w), K,
+                               int(flags), C.byref(h))
     _check(rc, "gbrt_scene_upload")
     return h.value
 
@@ -247,13 +280,17 @@ def gbrt_scene_update(ctx, scene, spheres, cylinders, flags=None):
     numpy arrays (host; pinned ones are read asynchronously)."""
     if flags is None:
         flags = HOST_PTRS if isinstance(spheres, np.ndarray) else DEVICE_PTRS
-    if flags == HOST_PTRS:
+    host = flags == HOST_PTRS
+    if host:
         if not (isinstance(spheres, np.ndarray) and spheres.dtype == np.float32 and spheres.flags.c_contiguous):
             spheres = np.ascontiguousarray(spheres, np.float32)
         if not (isinstance(cylinders, np.ndarray) and cylinders.dtype == np.float32
                 and cylinders.flags.c_contiguous):
             cylinders = np.ascontiguousarray(cylinders, np.float32)
-    return _check(lib.gbrt_scene_update(ctx, scene, ptr(spheres), ptr(cylinders), int(flags)), "gbrt_scene_update")
+    info = gbrt_scene_info(scene)
+    w = "gbrt_scene_update"
+    return _check(lib.gbrt_scene_update(ctx, scene, _buf(spheres, 16 * info["n_spheres"], host, w),
+                                        _buf(cylinders, 28 * info["n_cylinders"], host, w), int(flags)), w)
 
 
 MB_FP32_FMA, MB_FP64_FMA, MB_L2_READ = 0, 1, 2
@@ -276,9 +313,13 @@ def gbrt_render(ctx, scene, grid, camera, width, height, ao_samples, lights, par
     cam = camera if isinstance(camera, gbrt_camera) else make_camera(camera)
     li = lights if isinstance(lights, gbrt_lights) else make_lights(lights)
     pa = params if isinstance(params, gbrt_params) else make_params(params)
+    host = bool(pa.out_flags & HOST_PTRS)
+    rgb_b, px_b = _frame_bytes(cam, width, height, pa)
+    w = "gbrt_render"
     rc = lib.gbrt_render(ctx, scene, grid, C.byref(cam), int(width), int(height), int(ao_samples), C.byref(li),
-                         C.byref(pa), ptr(out_rgb), ptr(out_hit_ids), ptr(out_ao_visible))
-    return _check(rc, "gbrt_render")
+                         C.byref(pa), _buf(out_rgb, rgb_b, host, w), _buf(out_hit_ids, px_b, host, w),
+                         _buf(out_ao_visible, px_b, host, w))
+    return _check(rc, w)
 
 
 def gbrt_render_batch(ctx, items, flags=0):
@@ -298,21 +339,28 @@ def gbrt_render_noalloc(scene, grid, camera, width, height, ao_samples, lights, 
     li = lights if isinstance(lights, gbrt_lights) else make_lights(lights)
     pa = params if isinstance(params, gbrt_params) else make_params(params)
     s = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+    rgb_b, px_b = _frame_bytes(cam, width, height, pa)
+    w = "gbrt_render_noalloc"
     rc = lib.gbrt_render_noalloc(scene, grid, C.byref(cam), int(width), int(height), int(ao_samples), C.byref(li),
-                                 C.byref(pa), ptr(out_rgb), ptr(out_hit_ids), ptr(out_ao_visible), s)
-    return _check(rc, "gbrt_render_noalloc")
+                                 C.byref(pa), _buf(out_rgb, rgb_b, False, w), _buf(out_hit_ids, px_b, False, w),
+                                 _buf(out_ao_visible, px_b, False, w), s)
+    return _check(rc, w)
 
 
 def gbrt_ao_probe(ctx, scene, grid, pts, nrm, ao_samples, params, out_visibility):
     pa = params if isinstance(params, gbrt_params) else make_params(params)
-    rc = lib.gbrt_ao_probe(ctx, scene, grid, ptr(pts), ptr(nrm), int(pts.shape[0]), int(ao_samples), C.byref(pa),
-                           ptr(out_visibility))
-    return _check(rc, "gbrt_ao_probe")
+    n = int(pts.shape[0])
+    w = "gbrt_ao_probe"
+    rc = lib.gbrt_ao_probe(ctx, scene, grid, _buf(pts, 24 * n, False, w), _buf(nrm, 24 * n, False, w), n,
+                           int(ao_samples), C.byref(pa), _buf(out_visibility, 4 * n, False, w))
+    return _check(rc, w)
 
 
 def gbrt_philox4x32_10(ctx, ctr, key, out):
-    return _check(lib.gbrt_philox4x32_10(ctx, ptr(ctr), ptr(key), int(ctr.shape[0]), ptr(out)),
-                  "gbrt_philox4x32_10")
+    n = int(ctr.shape[0])
+    w = "gbrt_philox4x32_10"
+    return _check(lib.gbrt_philox4x32_10(ctx, _buf(ctr, 16 * n, False, w), _buf(key, 8 * n, False, w), n,
+                                         _buf(out, 16 * n, False, w)), w)
 
 
 def gbrt_set_tuning(ctx, tile_w=8, tile_h=4, block=256, ctas_per_sm=0, refill=16):
@@ -356,7 +404,10 @@ def make_item(scene, grid, camera, width, height, ao_samples, lights, params, ou
     it.width, it.height, it.ao_samples = int(width), int(height), int(ao_samples)
     it.lights = lights if isinstance(lights, gbrt_lights) else make_lights(lights)
     it.params = params if isinstance(params, gbrt_params) else make_params(params)
-    it.out_rgb, it.out_hit_ids, it.out_ao_visible = ptr(out_rgb), ptr(out_hit_ids), ptr(out_ao_visible)
+    rgb_b, px_b = _frame_bytes(it.camera, width, height, it.params)
+    w = "make_item"
+    it.out_rgb, it.out_hit_ids, it.out_ao_visible = (_buf(out_rgb, rgb_b, False, w), _buf(out_hit_ids, px_b, False, w),
+                                                     _buf(out_ao_visible, px_b, False, w))
     return it
 
 

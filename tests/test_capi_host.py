@@ -95,3 +95,29 @@ def test_create_without_device_reports_edevice(G):
         pytest.skip("a device is present")
     h = C.c_void_p()
     assert G.lib.gbrt_create(C.byref(h), 0, None) == G.EDEVICE
+
+
+def test_binding_checks_buffers_before_the_call(G):
+    # the binding passes only dense buffers of the right memory kind and size
+    import numpy as np
+    import torch
+    a = np.zeros((4, 3), np.float32)
+    assert G._buf(a, 48, True, "t") == a.ctypes.data
+    assert G._buf(None, 48, True, "t") is None and G._buf(1234, 48, True, "t") == 1234
+    for bad, host in ((a, False),                       # numpy arrays are host memory
+                      (a[:, :2], True),                 # not dense
+                      (np.zeros(11, np.float32), True),  # 44 bytes < 48
+                      (torch.zeros(12), False),         # a CPU tensor where device memory is expected
+                      (torch.zeros(4, 3).t(), True)):   # not contiguous
+        with pytest.raises(G.GbrtError) as e:
+            G._buf(bad, 48, host, "t")
+        assert e.value.code == G.EINVAL
+    t = torch.zeros(12)
+    assert G._buf(t, 48, True, "t") == t.data_ptr()   # a CPU tensor is host memory
+    cam = G.make_camera(type("Cam", (), dict(kind=0, aa=2, eye=(0, 0, 1), dir=(0, 0, -1), up=(0, 1, 0),
+                                              right=(1, 0, 0), half_w=1.0, half_h=1.0))())
+    p = G.gbrt_params()
+    p.precision = G.FP64
+    assert G._frame_bytes(cam, 5, 3, p) == (5 * 3 * 3 * 8, 5 * 3 * 4 * 4)
+    p.precision = G.FP32
+    assert G._frame_bytes(cam, -5, 3, p) == (0, 0)
