@@ -690,6 +690,9 @@ def main():
         cpu = {"value": round(s["rays"] / s["seconds"] / 1e6, 4), "unit": "Mrays/s", "cores": s["cores"],
                "kind": "oracle", "sample": f"{s['rows']} evenly spaced rows ({s['pixels']} px, {s['rays']} rays) "
                                            f"of the 965x1137 frame, FP64 grid walk, lambda {lam}"}
+        s1 = oracle_sample(w, lam, budget_s=4.0, threads=1)
+        cpu["single_core"] = {"value": round(s1["rays"] / s1["seconds"] / 1e6, 4), "cores": 1,
+                              "sample": f"{s1['rows']} evenly spaced rows ({s1['rays']} rays)"}
         if phases:
             # dominant kernel: the AO walk; its algorithmic work per launch is the
             # AO rays of one frame x the oracle's AO flops per ray (same grid lambda)
