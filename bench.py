@@ -693,6 +693,12 @@ def main():
         s1 = oracle_sample(w, lam, budget_s=4.0, threads=1)
         cpu["single_core"] = {"value": round(s1["rays"] / s1["seconds"] / 1e6, 4), "cores": 1,
                               "sample": f"{s1['rows']} evenly spaced rows ({s1['rays']} rays)"}
+        if not args.no_extras and args.workload == "paper_1mp":
+            w17 = S.paper_17mp(precision=p.precision, scene=w.scene)
+            s17 = oracle_sample(w17, lam, budget_s=20.0)
+            cpu["17.6MP"] = {"value": round(s17["rays"] / s17["seconds"] / 1e6, 4), "cores": s17["cores"],
+                             "seconds": round(s17["seconds"], 2),
+                             "sample": f"{s17['rows']} evenly spaced rows of 4548 ({s17['rays']} rays)"}
         if phases:
             # dominant kernel: the AO walk; its algorithmic work per launch is the
             # AO rays of one frame x the oracle's AO flops per ray (same grid lambda)
