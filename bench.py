@@ -144,6 +144,10 @@ class ClockSampler:
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            # the timed region starts once the sampler is running
+            t_end = time.time() + 3.0
+            while not self.lines and time.time() < t_end and self.proc.poll() is None:
+                time.sleep(0.01)
         except (OSError, ValueError):
             self.proc = None
         return self
@@ -226,8 +230,10 @@ def run_reference(args, w):
     import oracle
     lam = args.lam
     times, rays = [], 0
+    # each step a bounded row sample: the whole run stays within a few minutes
+    budget = min(args.ref_budget, 150.0 / (args.warmup + args.steps))
     for k in range(args.warmup + args.steps):
-        s = oracle_sample(w, lam, budget_s=args.ref_budget)
+        s = oracle_sample(w, lam, budget_s=budget)
         if k >= args.warmup:
             times.append(s["seconds"])
             rays += s["rays"]
@@ -408,7 +414,8 @@ def run_serve(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=0,
+                    help="timed steps (0: about a second of device time for the workload)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="paper_1mp", help="paper_1mp | paper_17mp | small | orbit64")
@@ -426,6 +433,10 @@ def main():
     ap.add_argument("--hbm-gb", type=float, default=16.0, help="serve: HBM budget for outputs")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.steps <= 0:
+        # a timed region of about a second, so the clock sampler (every 200 ms)
+        # sees it several times
+        args.steps = {"paper_1mp": 500, "small": 500, "paper_17mp": 40, "orbit64": 12}.get(args.workload, 20)
     if args.workload == "serve" and args.impl == "ours":
         run_serve(args)
         return

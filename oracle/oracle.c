@@ -735,8 +735,9 @@ int oracle_ao_probe(int64_t S, const double* sph, int64_t C, const double* cyl, 
     oworld w;
     if (world_init(&w, S, sph, C, cyl, NULL, NULL, 0, mode, lambda)) return -1;
 #ifdef _OPENMP
-    if (nthreads > 0) omp_set_num_threads(nthreads);
-#pragma omp parallel for schedule(dynamic, 4)
+    /* the thread count applies to this call only (0: all cores) */
+    const int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 4) num_threads(nt)
 #endif
     for (int64_t i = 0; i < npts; ++i) {
         const double* p = pts + 3 * i;
@@ -791,8 +792,8 @@ int oracle_render(int64_t S, const double* sph, int64_t C, const double* cyl,
     int64_t tot[16];
     memset(tot, 0, sizeof(tot));
 #ifdef _OPENMP
-    if (nthreads > 0) omp_set_num_threads(nthreads);
-#pragma omp parallel
+    const int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#pragma omp parallel num_threads(nt)
 #endif
     {
         int64_t loc[16];
