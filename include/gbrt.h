@@ -42,7 +42,9 @@ extern "C" {
 #define GBRT_API
 #endif
 
-#define GBRT_VERSION 3
+/* 4: host-output copies run on a stream of the context's own (complete at
+ *    gbrt_sync); a grid must belong to the rendered scene. */
+#define GBRT_VERSION 4
 
 /* ---- error codes ---- */
 #define GBRT_OK 0
