@@ -222,28 +222,28 @@ __device__ __forceinline__ bool clip_grid(const GridDev& g, V3<R> o, V3<R> d, R 
 }
 
 // Amanatides & Woo (1987) traversal state: the current cell's index, per
-// axis the steps left before the grid ends, the index change of one step, the
-// t of the next boundary crossing and the t between crossings.
+// axis the index change of one step, the t of the next boundary crossing and
+// the t between crossings; the end of the clipped interval and the number of
+// cells (the walk's bounds).
 template <class R>
 struct Walk {
-    int rx, ry, rz;
     int stx, sty, stz;
     R tnx, tny, tnz;
     R tdx, tdy, tdz;
     R t1;
     int cell;
     int left;
+    unsigned ncells;
 };
 
 // One axis of the walk's set-up (selects, not branches: lanes differ in the
 // signs of their directions). Moving up the axis the next boundary is the
 // cell's upper face, moving down its lower face; a zero component never steps.
 template <class R>
-__device__ __forceinline__ void axis_setup(const GridDev& g, int k, R o, R d, R inv, int c, int stride, int& r,
-                                           int& st, R& tn, R& td) {
+__device__ __forceinline__ void axis_setup(const GridDev& g, int k, R o, R d, R inv, int c, int stride, int& st,
+                                           R& tn, R& td) {
     const bool up = d > R(0), down = d < R(0);
     const R h = GridP<R>::h(g, k);
-    r = up ? g.n[k] - 1 - c : (down ? c : 0);
     st = up ? stride : (down ? -stride : 0);
     const R face = GridP<R>::lo(g, k) + R(up ? c + 1 : c) * h;
     tn = (up || down) ? (face - o) * inv : Num<R>::inf();
@@ -266,9 +266,10 @@ __device__ __forceinline__ bool walk_start(const GridDev& g, V3<R> o, V3<R> d, R
     V3<R> p = madd(o, t0, d);
     const int cx = cell_of(g, 0, p.x), cy = cell_of(g, 1, p.y), cz = cell_of(g, 2, p.z);
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-    axis_setup(g, 0, o.x, d.x, inv.x, cx, 1, w.rx, w.stx, w.tnx, w.tdx);
-    axis_setup(g, 1, o.y, d.y, inv.y, cy, nx, w.ry, w.sty, w.tny, w.tdy);
-    axis_setup(g, 2, o.z, d.z, inv.z, cz, nx * ny, w.rz, w.stz, w.tnz, w.tdz);
+    axis_setup(g, 0, o.x, d.x, inv.x, cx, 1, w.stx, w.tnx, w.tdx);
+    axis_setup(g, 1, o.y, d.y, inv.y, cy, nx, w.sty, w.tny, w.tdy);
+    axis_setup(g, 2, o.z, d.z, inv.z, cz, nx * ny, w.stz, w.tnz, w.tdz);
+    w.ncells = (unsigned)g.ncells;
     w.t1 = t1;
     w.cell = (cz * ny + cy) * nx + cx;
     w.left = nx + ny + nz + 3;
@@ -282,9 +283,17 @@ __device__ __forceinline__ R walk_cell_exit(const Walk<R>& w) {
 }
 
 // Step to the next cell (ties: x, then y, then z). False when the walk leaves
-// the grid or the clipped interval; sets *overflow past the step bound. Written
-// with selects rather than a branch per axis: the lanes of a warp step along
-// different axes.
+// the clipped interval or the grid's index range; sets *overflow past the step
+// bound. Written with selects rather than a branch per axis: the lanes of a
+// warp step along different axes.
+//
+// The clipped interval ends inside the grid, so in exact arithmetic no step
+// leaves it. Rounding in the accumulated crossings can carry the last one or
+// few steps just past the grid's edge, into a cell of another row or out of
+// the index range; the range check ends the walk, and the cells of another row
+// cost tests but change no result: every object the ray meets has its hit
+// point inside the grid, in a cell the walk visits before, and a test of any
+// other object finds only true intersections.
 template <class R>
 __device__ __forceinline__ bool walk_next(Walk<R>& w, bool& overflow) {
     if (--w.left <= 0) {
@@ -295,16 +304,12 @@ __device__ __forceinline__ bool walk_next(Walk<R>& w, bool& overflow) {
     const bool by = !bx && w.tny <= w.tnz;
     const bool bz = !bx && !by;
     const R tn = bx ? w.tnx : (by ? w.tny : w.tnz);
-    const int r = bx ? w.rx : (by ? w.ry : w.rz);
-    if (tn > w.t1 || r <= 0) return false;
-    w.rx -= bx ? 1 : 0;
-    w.ry -= by ? 1 : 0;
-    w.rz -= bz ? 1 : 0;
+    if (tn > w.t1) return false;
     w.tnx = bx ? w.tnx + w.tdx : w.tnx;
     w.tny = by ? w.tny + w.tdy : w.tny;
     w.tnz = bz ? w.tnz + w.tdz : w.tnz;
     w.cell += bx ? w.stx : (by ? w.sty : w.stz);
-    return true;
+    return (unsigned)w.cell < w.ncells;
 }
 
 // ---------------------------------------------------------------- traversal
