@@ -309,6 +309,24 @@ def test_asynchronous_host_outputs(G, R):
         assert np.array_equal(o[0], ref[0].cpu().numpy()), k
         assert np.array_equal(o[1], ref[1].cpu().numpy().view(np.uint32)), k
         assert np.array_equal(o[2], ref[2].cpu().numpy().view(np.uint32)), k
+    # a change of the context's stream between asynchronous renders: the
+    # copies of the earlier ones still complete before the next gbrt_sync
+    side = torch.cuda.Stream()
+    outs2 = []
+    for k, strm in enumerate((None, side, None)):
+        if strm is not None:
+            G.gbrt_set_stream(R.ctx, strm)
+        p = S.Params(ao_samples=5, seed=30 + k, frame=k)
+        o = torch.empty((50, 70, 3), dtype=torch.float32).pin_memory().numpy()
+        outs2.append((p, o))
+        G.gbrt_render(R.ctx, scene, grid, cam, W, H, 5, S.default_lights(),
+                      G.make_params(p, out_flags=G.HOST_PTRS | G.HOST_ASYNC), o)
+    G.gbrt_set_stream(R.ctx, R.stream)
+    G.gbrt_sync(R.ctx)
+    for p, o in outs2:
+        ref = R.render(scene, grid, cam, W, H, S.default_lights(), p)[0]
+        G.gbrt_sync(R.ctx)
+        assert np.array_equal(o, ref.cpu().numpy())
     with pytest.raises(G.GbrtError):  # asynchronous outputs must be host outputs
         G.gbrt_render(R.ctx, scene, grid, cam, W, H, 6, S.default_lights(),
                       G.make_params(frames[0], out_flags=G.HOST_ASYNC), torch.empty((H, W, 3), device="cuda"))
