@@ -165,29 +165,49 @@ __device__ __forceinline__ bool cell_reached(const float4* obj, int64_t id, cons
     return box_dist2(A.x + sm * B.x, A.y + sm * B.y, A.z + sm * B.z, lo, hi) <= lim * lim;
 }
 
+// Count and scatter run one warp per object (grid-stride over objects): the
+// lanes take the cells of the object's box in turn, k = 0, 1, ... with x
+// fastest, then y, then z, so an object's cells are tested in parallel.
+__device__ __forceinline__ void span_cell(const int c0[3], int nx, int ny, int k, int& x, int& y, int& z) {
+    x = c0[0] + k % nx;
+    y = c0[1] + (k / nx) % ny;
+    z = c0[2] + k / (nx * ny);
+}
+
+// Blocks of 256 threads for one warp per object over N objects.
+inline int object_warp_blocks(int64_t N) {
+    return (int)std::min<int64_t>((std::max<int64_t>(N, 1) + 7) / 8, 1 << 20);
+}
+
 // Count pass. When an object's box spans at most 64 cells, the cells its shape
-// reaches are also recorded as bits (x fastest, then y, then z) in reach[id],
-// so the scatter pass need not repeat the test; wider objects get all-ones
-// and are tested again there.
+// reaches are also recorded as bits k in reach[id], so the scatter pass need
+// not repeat the test; wider objects get all-ones and are tested again there.
 __global__ void __launch_bounds__(256) k_grid_count(const float4* aabb, const float4* obj, int64_t N,
                                                      const BuildP* bp, uint32_t* counts,
                                                      unsigned long long* reach) {
-    int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (id >= N) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     const BuildP p = *bp;
-    int c0[3], c1[3];
-    cell_range(aabb, id, p, c0, c1);
-    const int span = (c1[0] - c0[0] + 1) * (c1[1] - c0[1] + 1) * (c1[2] - c0[2] + 1);
-    unsigned long long bits = 0ull;
-    int k = 0;
-    for (int z = c0[2]; z <= c1[2]; ++z)
-        for (int y = c0[1]; y <= c1[1]; ++y)
-            for (int x = c0[0]; x <= c1[0]; ++x, ++k)
-                if (cell_reached(obj, id, p, x, y, z)) {
-                    atomicAdd(counts + ((int64_t)z * p.n[1] + y) * p.n[0] + x, 1u);
-                    if (k < 64) bits |= 1ull << k;
-                }
-    reach[id] = span <= 64 ? bits : ~0ull;
+    for (int64_t id = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; id < N; id += warps) {
+        int c0[3], c1[3];
+        cell_range(aabb, id, p, c0, c1);
+        const int nx = c1[0] - c0[0] + 1, ny = c1[1] - c0[1] + 1;
+        const int span = nx * ny * (c1[2] - c0[2] + 1);
+        unsigned long long bits = 0ull;
+        for (int base = 0; base < span; base += 32) {
+            const int k = base + lane;
+            bool hit = false;
+            if (k < span) {
+                int x, y, z;
+                span_cell(c0, nx, ny, k, x, y, z);
+                hit = cell_reached(obj, id, p, x, y, z);
+                if (hit) atomicAdd(counts + ((int64_t)z * p.n[1] + y) * p.n[0] + x, 1u);
+            }
+            const unsigned got = __ballot_sync(0xffffffffu, hit);
+            if (base < 64) bits |= (unsigned long long)got << base;
+        }
+        if (lane == 0) reach[id] = span <= 64 ? bits : ~0ull;
+    }
 }
 
 // Items past `items_cap` are dropped (a device-side rebuild that outgrew its
@@ -196,23 +216,26 @@ __global__ void __launch_bounds__(256) k_grid_scatter(const float4* aabb, const 
                                                        const BuildP* bp, const unsigned long long* reach,
                                                        const uint2* cells, uint32_t* cursor, uint32_t* items,
                                                        uint64_t items_cap) {
-    int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (id >= N) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     const BuildP p = *bp;
-    int c0[3], c1[3];
-    cell_range(aabb, id, p, c0, c1);
-    const unsigned long long bits = reach[id];
-    const bool recorded = bits != ~0ull;
-    int k = 0;
-    for (int z = c0[2]; z <= c1[2]; ++z)
-        for (int y = c0[1]; y <= c1[1]; ++y)
-            for (int x = c0[0]; x <= c1[0]; ++x, ++k) {
-                if (recorded ? !((bits >> k) & 1ull) : !cell_reached(obj, id, p, x, y, z)) continue;
-                int64_t c = ((int64_t)z * p.n[1] + y) * p.n[0] + x;
-                uint32_t slot = atomicAdd(cursor + c, 1u);
-                const uint64_t at = (uint64_t)cells[c].x + slot;
-                if (at < items_cap) items[at] = (uint32_t)id;
-            }
+    for (int64_t id = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; id < N; id += warps) {
+        int c0[3], c1[3];
+        cell_range(aabb, id, p, c0, c1);
+        const int nx = c1[0] - c0[0] + 1, ny = c1[1] - c0[1] + 1;
+        const int span = nx * ny * (c1[2] - c0[2] + 1);
+        const unsigned long long bits = reach[id];
+        const bool recorded = bits != ~0ull;  // then span <= 64
+        for (int k = lane; k < span; k += 32) {
+            int x, y, z;
+            span_cell(c0, nx, ny, k, x, y, z);
+            if (recorded ? !((bits >> k) & 1ull) : !cell_reached(obj, id, p, x, y, z)) continue;
+            const int64_t c = ((int64_t)z * p.n[1] + y) * p.n[0] + x;
+            const uint32_t slot = atomicAdd(cursor + c, 1u);
+            const uint64_t at = (uint64_t)cells[c].x + slot;
+            if (at < items_cap) items[at] = (uint32_t)id;
+        }
+    }
 }
 
 // Radius of the sphere about `ctr` that holds every object: sphere |c - ctr| + r,
@@ -638,7 +661,7 @@ int grid_build(Ctx* ctx, const Scene* s, float lambda, Grid* g) {
         BuildAux* d_aux = (BuildAux*)(sums + nb + 2);
         GB_TRY(cudaMemcpyAsync(d_aux, &a, sizeof(a), cudaMemcpyHostToDevice, ctx->stream));
         if (N > 0) {
-            k_grid_count<<<(int)((N + 255) / 256), 256, 0, ctx->stream>>>(s->aabb, s->obj, N, &d_aux->p, counts,
+            k_grid_count<<<object_warp_blocks(N), 256, 0, ctx->stream>>>(s->aabb, s->obj, N, &d_aux->p, counts,
                                                                           reach);
             k_bound_radius<<<(int)((N + 255) / 256), 256, 0, ctx->stream>>>(s->obj64, N, d_aux->ctr, &d_aux->rbits);
             ctx->launches += 2;
@@ -662,7 +685,7 @@ int grid_build(Ctx* ctx, const Scene* s, float lambda, Grid* g) {
         if (N > 0) {
             cursor = counts;  // reuse as per-cell fill cursor
             GB_TRY(cudaMemsetAsync(cursor, 0, (size_t)nc * sizeof(uint32_t), ctx->stream));
-            k_grid_scatter<<<(int)((N + 255) / 256), 256, 0, ctx->stream>>>(s->aabb, s->obj, N, &d_aux->p, reach,
+            k_grid_scatter<<<object_warp_blocks(N), 256, 0, ctx->stream>>>(s->aabb, s->obj, N, &d_aux->p, reach,
                                                                             g->cells,
                                                                             cursor, g->items, (uint64_t)g->refs);
             k_cell_sort<<<(int)((nc + 255) / 256), 256, 0, ctx->stream>>>(g->cells, nc, g->items,
@@ -825,7 +848,7 @@ int grid_rebuild(Ctx* ctx, const Scene* s, Grid* g) {
     if (cudaMemsetAsync(g->d_counts, 0, (size_t)nc * sizeof(uint32_t), st) != cudaSuccess) return GBRT_EDEVICE;
     k_grid_geometry<<<1, 32, 0, st>>>(s->d_box, N, g->lambda, nc, g->cells, g->items, g->d_geom, g->d_aux);
     if (N > 0) {
-        k_grid_count<<<blocksN, 256, 0, st>>>(s->aabb, s->obj, N, &g->d_aux->p, g->d_counts, g->d_reach);
+        k_grid_count<<<object_warp_blocks(N), 256, 0, st>>>(s->aabb, s->obj, N, &g->d_aux->p, g->d_counts, g->d_reach);
         k_bound_radius<<<blocksN, 256, 0, st>>>(s->obj64, N, g->d_aux->ctr, &g->d_aux->rbits);
     }
     k_scan_reduce<<<(int)nb, SCAN_T, 0, st>>>(g->d_counts, nc, g->d_sums);
@@ -833,7 +856,7 @@ int grid_rebuild(Ctx* ctx, const Scene* s, Grid* g) {
     k_scan_apply<<<(int)nb, SCAN_T, 0, st>>>(g->d_counts, nc, g->d_sums, g->cells);
     if (N > 0) {
         if (cudaMemsetAsync(g->d_counts, 0, (size_t)nc * sizeof(uint32_t), st) != cudaSuccess) return GBRT_EDEVICE;
-        k_grid_scatter<<<blocksN, 256, 0, st>>>(s->aabb, s->obj, N, &g->d_aux->p, g->d_reach, g->cells, g->d_counts,
+        k_grid_scatter<<<object_warp_blocks(N), 256, 0, st>>>(s->aabb, s->obj, N, &g->d_aux->p, g->d_reach, g->cells, g->d_counts,
                                                 g->items,
                                                 (uint64_t)g->items_cap);
         // no per-cell sort: no result depends on the order of a cell's ids
