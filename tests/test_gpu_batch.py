@@ -149,3 +149,48 @@ def test_orbit64_graph_batch_sampled_vs_oracle(G, oracle):
                 assert_parity(st, f"orbit frame {k} {W}x{H} spp {f['spp']}")
                 assert st["vis_eq"] >= 0.995, (k, st)
         r.free(scene, grid)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_random_batches_equal_solo(G, seed):
+    # random mixes: two scenes, both precisions, supersampling, shadows, row
+    # bands and ragged sizes in one batch (graph-replayed or not) give exactly
+    # the solo renders
+    import dataclasses
+    import torch
+    rng = np.random.default_rng(500 + seed)
+    scenes = [S.globule(400, 380, 13.0, seed=seed), S.globule(150, 90, 8.0, seed=seed + 7)]
+    lights = S.default_lights()
+    with G.Renderer(0) as r:
+        handles = [r.upload(sc, lam=float(rng.choice([1.0, 2.0, 8.0]))) for sc in scenes]
+        items, outs, solo = [], [], []
+        for k in range(int(rng.integers(5, 11))):
+            si = int(rng.integers(0, 2))
+            sc, (scene, grid) = scenes[si], handles[si]
+            W, H = int(rng.integers(1, 80)), int(rng.integers(1, 60))
+            m = int(rng.choice([1, 1, 2]))
+            cam = dataclasses.replace(S.ortho_camera(sc, W, H, angle_deg=float(rng.uniform(0, 360))), aa=m)
+            prec = S.PRECISION_FP64 if rng.random() < 0.3 else S.PRECISION_FP32
+            p = S.Params(ao_samples=int(rng.integers(0, 12)), seed=int(rng.integers(0, 1 << 30)), frame=k,
+                         precision=prec, shadows=bool(rng.random() < 0.5))
+            ref = r.render(scene, grid, cam, W, H, lights, p, ids=True, vis=True)
+            solo.append(tuple(x.clone() for x in ref))
+            dt = torch.float64 if prec == S.PRECISION_FP64 else torch.float32
+            o = (torch.full((H, W, 3), -1, dtype=dt, device="cuda"),
+                 torch.full((m * H, m * W), -7, dtype=torch.int32, device="cuda"),
+                 torch.full((m * H, m * W), -7, dtype=torch.int32, device="cuda"))
+            outs.append(o)
+            if H > 2 and rng.random() < 0.5:
+                cut = int(rng.integers(1, H))
+                items.append(G.make_item(scene, grid, cam, W, H, p.ao_samples, lights, p, *o, rows=(cut, H)))
+                items.append(G.make_item(scene, grid, cam, W, H, p.ao_samples, lights, p, *o, rows=(0, cut)))
+            else:
+                items.append(G.make_item(scene, grid, cam, W, H, p.ao_samples, lights, p, *o))
+        order = rng.permutation(len(items))
+        flags = G.BATCH_GRAPH if seed % 2 else 0
+        for _ in range(2 if flags else 1):
+            G.gbrt_render_batch(r.ctx, [items[i] for i in order], flags)
+            G.gbrt_sync(r.ctx)
+        for k, (a, b) in enumerate(zip(solo, outs)):
+            for x, y in zip(a, b):
+                assert torch.equal(x, y), k
