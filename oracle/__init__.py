@@ -33,12 +33,12 @@ def lib():
         L.oracle_cosine_dir.argtypes = [P, f64, f64, P]
         L.oracle_hit_sphere.argtypes = [P, P, P, f64, f64, f64, P, P]
         L.oracle_hit_cylinder.argtypes = [P, P, P, P, f64, f64, f64, P, P]
-        L.oracle_nearest.argtypes = [i64, P, i64, P, i32, f64, i64, P, P, f64, f64, P, P, P, P]
+        L.oracle_nearest.argtypes = [i64, P, i64, P, i32, f64, i64, P, P, f64, f64, P, P, P, P, P, P]
         L.oracle_grid_walk.argtypes = [i64, P, i64, P, f64, P, P, f64, f64, i64, P, P]
         L.oracle_grid_info.argtypes = [i64, P, i64, P, f64, P, P, P]
         L.oracle_ao_probe.argtypes = [i64, P, i64, P, i32, f64, i64, P, P, i32, u64, u32, f64, f64, P, i32]
         L.oracle_render.argtypes = [i64, P, i64, P, P, P, i32, P, i32, i32, P, P, i32, P,
-                                    i32, u64, u32, i32, f64, i64, P, P, P, P, P, P, P, i32]
+                                    i32, u64, u32, i32, f64, i64, P, P, P, P, P, P, P, P, P, i32]
         L.oracle_max_threads.restype = C.c_int
         _lib = L
     return _lib
@@ -93,8 +93,8 @@ def cosine_dir(n, u1, u2):
 
 
 class _Graze(C.Structure):
-    _fields_ = [("disc_rel", C.c_double), ("t_close", C.c_double), ("end_mrg", C.c_double),
-                ("t_end", C.c_double)]
+    _fields_ = [("disc_rel", C.c_double), ("t_close", C.c_double), ("t_near", C.c_double),
+                ("s_out", C.c_double), ("end_mrg", C.c_double * 2), ("t_end", C.c_double * 2)]
 
 
 def hit_sphere(o, d, c, r, tmin=0.0, tmax=math.inf):
@@ -125,8 +125,12 @@ def _scene_arrays(scene):
     return sph, cyl, col, pal
 
 
-def nearest(scene, orig, dirs, mode="brute", lam=1.0, tmin=0.0, tmax=math.inf):
-    """Nearest hit (id, t, grazing flag) of explicit rays; directions are normalised."""
+def nearest_detail(scene, orig, dirs, mode="brute", lam=1.0, tmin=0.0, tmax=math.inf):
+    """Nearest hits of explicit rays (directions are normalised), as a dict:
+    id, t, grazing; for grazing rays id2 (the runner-up: second-nearest
+    distinct hit) and idg (the object of the nearest grazing encounter), MISS
+    where there is none and on non-grazing rays; counters (cells, sphere
+    tests, cylinder tests)."""
     sph, cyl, _, _ = _scene_arrays(scene)
     o = _f64(orig, (-1, 3))
     d = _f64(dirs, (-1, 3))
@@ -135,12 +139,21 @@ def nearest(scene, orig, dirs, mode="brute", lam=1.0, tmin=0.0, tmax=math.inf):
     ids = np.zeros(n, np.uint32)
     ts = np.zeros(n)
     gz = np.zeros(n, np.uint8)
+    id2 = np.zeros(n, np.uint32)
+    idg = np.zeros(n, np.uint32)
     cnt = np.zeros(3, np.int64)
     rc = lib().oracle_nearest(sph.shape[0], _p(sph), cyl.shape[0], _p(cyl), MODES[mode], float(lam), n,
-                              _p(o), _p(d), float(tmin), float(tmax), _p(ids), _p(ts), _p(gz), _p(cnt))
+                              _p(o), _p(d), float(tmin), float(tmax), _p(ids), _p(ts), _p(gz), _p(id2), _p(idg),
+                              _p(cnt))
     if rc:
         raise RuntimeError("oracle_nearest failed")
-    return ids, ts, gz.astype(bool), cnt
+    return dict(id=ids, t=ts, grazing=gz.astype(bool), id2=id2, idg=idg, counters=cnt)
+
+
+def nearest(scene, orig, dirs, mode="brute", lam=1.0, tmin=0.0, tmax=math.inf):
+    """Nearest hit (id, t, grazing flag, counters) of explicit rays; directions are normalised."""
+    r = nearest_detail(scene, orig, dirs, mode=mode, lam=lam, tmin=tmin, tmax=tmax)
+    return r["id"], r["t"], r["grazing"], r["counters"]
 
 
 def grid_walk(scene, o, d, lam=1.0, tmin=0.0, tmax=math.inf, max_out=1 << 16):
@@ -221,8 +234,9 @@ def render(scene, camera, width, height, lights, params, pixels=None, mode="grid
     Returns a dict with rgb [n,3] float64 per pixel and, per sub-sample
     (n m^2 entries, pixel-major, then sub-row b, then sub-column a; m = the
     camera's sub-pixel grid side, 1 without supersampling): id uint32
-    (0xFFFFFFFF = miss), t, vis (unoccluded AO samples), grazing bool; and a
-    counters dict.
+    (0xFFFFFFFF = miss), t, vis (unoccluded AO samples), grazing bool, and for
+    grazing sub-samples id2 (the runner-up) and idg (the object of the
+    nearest grazing encounter), MISS where there is none; and a counters dict.
     """
     sph, cyl, col, pal = _scene_arrays(scene)
     cam = camera_vector(camera)
@@ -242,12 +256,15 @@ def render(scene, camera, width, height, lights, params, pixels=None, mode="grid
     ts = np.zeros(nsub)
     vis = np.zeros(nsub, np.int32)
     gz = np.zeros(nsub, np.uint8)
+    id2 = np.zeros(nsub, np.uint32)
+    idg = np.zeros(nsub, np.uint32)
     cnt = np.zeros(16, np.int64)
     rc = lib().oracle_render(sph.shape[0], _p(sph), cyl.shape[0], _p(cyl), _p(col), _p(pal), pal.shape[0],
                              _p(cam), int(width), int(height), _p(ldir), _p(lI), ldir.shape[0], _p(sp),
                              int(spp), int(params.seed), int(params.frame), MODES[mode], float(lam),
-                             npix, _p(pix), _p(rgb), _p(ids), _p(ts), _p(vis), _p(gz), _p(cnt), int(threads))
+                             npix, _p(pix), _p(rgb), _p(ids), _p(ts), _p(vis), _p(gz), _p(id2), _p(idg), _p(cnt),
+                             int(threads))
     if rc:
         raise RuntimeError(f"oracle_render failed ({rc})")
-    return dict(rgb=rgb, id=ids, t=ts, vis=vis, grazing=gz.astype(bool),
+    return dict(rgb=rgb, id=ids, t=ts, vis=vis, grazing=gz.astype(bool), id2=id2, idg=idg,
                 counters={k: int(cnt[i]) for i, k in enumerate(COUNTER_NAMES)})

@@ -133,12 +133,17 @@ static void normalize3(double v[3])
 /*   disc_rel : (r^2 - h^2)/r^2, h = closest distance of ray to the surface's */
 /*              generator (sphere centre / cylinder axis); < 0 means miss.   */
 /*   t_close  : ray parameter of that closest approach.                      */
-/*   end_mrg  : cylinders only, axial distance of the accepted root to the   */
-/*              nearer clip plane (in scene units); +inf otherwise.          */
+/*   t_near   : where a flip of the silhouette decision acts: the nearer     */
+/*              root when the ray meets the surface (disc >= 0), else t_close */
+/*   s_out    : cylinders only, how far the closest approach lies outside the */
+/*              segment along the axis (0 within it; 0 for spheres)          */
+/*   end_mrg[k], t_end[k] : cylinders only, for root k (0 near, 1 far) in   */
+/*              (tmin, tmax]: the axial distance of its point to the nearer  */
+/*              clip plane (scene units) and its t; +inf otherwise.          */
 /* ------------------------------------------------------------------------ */
 
 typedef struct {
-    double disc_rel, t_close, end_mrg, t_end;
+    double disc_rel, t_close, t_near, s_out, end_mrg[2], t_end[2];
 } graze_t;
 
 /* Sphere |p - c| = r, ray p = o + t d with |d| = 1. With f = o - c and
@@ -156,12 +161,15 @@ int oracle_hit_sphere(const double o[3], const double d[3], const double c[3], d
     if (g) {
         g->disc_rel = disc / (r * r);
         g->t_close = -b;
-        g->end_mrg = INFINITY;
-        g->t_end = INFINITY;
+        g->t_near = -b;
+        g->s_out = 0.0;
+        g->end_mrg[0] = g->end_mrg[1] = INFINITY;
+        g->t_end[0] = g->t_end[1] = INFINITY;
     }
     if (disc < 0.0) return 0;
     double sq = sqrt(disc);
     double t0 = -b - sq, t1 = -b + sq;
+    if (g) g->t_near = t0;
     if (t0 > tmin && t0 <= tmax) { *t_out = t0; return 1; }
     if (t1 > tmin && t1 <= tmax) { *t_out = t1; return 1; }
     return 0;
@@ -178,7 +186,11 @@ int oracle_hit_cylinder(const double o[3], const double d[3], const double p0[3]
 {
     double ax[3] = {p1[0] - p0[0], p1[1] - p0[1], p1[2] - p0[2]};
     double L = sqrt(dot3(ax, ax));
-    if (g) { g->disc_rel = -INFINITY; g->t_close = 0.0; g->end_mrg = INFINITY; g->t_end = INFINITY; }
+    if (g) {
+        g->disc_rel = -INFINITY; g->t_close = 0.0; g->t_near = 0.0; g->s_out = INFINITY;
+        g->end_mrg[0] = g->end_mrg[1] = INFINITY;
+        g->t_end[0] = g->t_end[1] = INFINITY;
+    }
     if (!(L > 0.0)) return 0;
     double a[3] = {ax[0] / L, ax[1] / L, ax[2] / L};
     double w[3] = {o[0] - p0[0], o[1] - p0[1], o[2] - p0[2]};
@@ -191,19 +203,23 @@ int oracle_hit_cylinder(const double o[3], const double d[3], const double p0[3]
     double m[3] = {wp[0] + tc * dp[0], wp[1] + tc * dp[1], wp[2] + tc * dp[2]};
     double h2 = dot3(m, m);
     double disc = r * r - h2;
-    if (g) { g->disc_rel = disc / (r * r); g->t_close = tc; }
+    if (g) {
+        double sc = wa + tc * da;
+        g->disc_rel = disc / (r * r);
+        g->t_close = tc;
+        g->t_near = tc;
+        g->s_out = fmax(0.0, fmax(-sc, sc - L));
+    }
     if (disc < 0.0) return 0;
     double half = sqrt(disc / A);
     double roots[2] = {tc - half, tc + half};
+    if (g) g->t_near = roots[0];
     int hit = 0;
     for (int k = 0; k < 2; ++k) {
         double t = roots[k];
         if (!(t > tmin && t <= tmax)) continue;
         double s = wa + t * da;
-        if (g) {
-            double em = fmin(fabs(s), fabs(L - s));
-            if (em < g->end_mrg) { g->end_mrg = em; g->t_end = t; }
-        }
+        if (g) { g->end_mrg[k] = fmin(fabs(s), fabs(L - s)); g->t_end[k] = t; }
         if (!hit && s >= 0.0 && s <= L) { *t_out = t; hit = 1; }
     }
     return hit;
@@ -453,7 +469,16 @@ typedef struct {
     double t1, t2;      /* nearest and second-nearest distinct hits */
     uint32_t id1, id2;
     double t_graze;     /* smallest t of a grazing encounter */
+    uint32_t id_graze;  /* the object of that encounter */
 } nearest_t;
+
+static void nearest_reset(nearest_t* nr)
+{
+    nr->t1 = nr->t2 = INFINITY;
+    nr->id1 = nr->id2 = OR_MISS;
+    nr->t_graze = INFINITY;
+    nr->id_graze = OR_MISS;
+}
 
 static void consider(const oscene* sc, int64_t id, const double o[3], const double d[3],
                      double tmin, double tmax, nearest_t* nr, ocount* cnt)
@@ -462,13 +487,28 @@ static void consider(const oscene* sc, int64_t id, const double o[3], const doub
     graze_t g;
     if (id < sc->S) cnt->sph++; else cnt->cyl++;
     int hit = hit_object(sc, id, o, d, tmin, tmax, &t, &g);
-    if (fabs(g.disc_rel) < GRAZE_DISC && g.t_close > tmin && g.t_close < nr->t_graze)
-        nr->t_graze = g.t_close;
+    double L = 0.0; /* a tube's length (clip-plane margin GRAZE_END (L + 1)) */
     if (id >= sc->S) {
         const double* c = sc->cyl + 7 * (id - sc->S);
         double ax[3] = {c[3] - c[0], c[4] - c[1], c[5] - c[2]};
-        double L = sqrt(dot3(ax, ax));
-        if (g.end_mrg < GRAZE_END * (L + 1.0) && g.t_end < nr->t_graze) nr->t_graze = g.t_end;
+        L = sqrt(dot3(ax, ax));
+    }
+    /* a silhouette decision within rounding of flipping, in front of the origin
+     * (for a tube: with the closest approach within the clip margin of the
+     * segment; elsewhere no root can count): it acts at the nearer root (at
+     * the closest approach when the ray misses) */
+    if (fabs(g.disc_rel) < GRAZE_DISC && g.t_close > tmin && g.s_out <= GRAZE_END * (L + 1.0) &&
+        g.t_near < nr->t_graze) {
+        nr->t_graze = g.t_near;
+        nr->id_graze = (uint32_t)id;
+    }
+    if (id >= sc->S) {
+        for (int k = 0; k < 2; ++k) {
+            if (g.end_mrg[k] < GRAZE_END * (L + 1.0) && g.t_end[k] < nr->t_graze) {
+                nr->t_graze = g.t_end[k];
+                nr->id_graze = (uint32_t)id;
+            }
+        }
     }
     if (!hit) return;
     uint32_t uid = (uint32_t)id;
@@ -504,6 +544,17 @@ static void nearest_grid(const oscene* sc, const ogrid* gr, const double o[3], c
         /* every object whose hit point lies in a visited cell has been tested */
         if (nr->id1 != OR_MISS && nr->t1 <= dda_cell_exit(&w)) break;
     } while (dda_next(gr, &w));
+    if (nr->id1 == OR_MISS) return;
+    /* Not part of the method's work (no counts): the cells entered before
+     * t1 (1 + GRAZE_TIE), so that a near-tie or grazing encounter just past
+     * the cell of the hit is seen as brute force sees it. */
+    ocount extra = {0, 0, 0};
+    const double t_lim = nr->t1 * (1.0 + GRAZE_TIE) + 1e-9;
+    while (dda_cell_exit(&w) <= t_lim && dda_next(gr, &w)) {
+        int64_t c = ((int64_t)w.c[2] * gr->n[1] + w.c[1]) * gr->n[0] + w.c[0];
+        for (int64_t i = gr->start[c]; i < gr->start[c + 1]; ++i)
+            consider(sc, gr->items[i], o, d, tmin, tmax, nr, &extra);
+    }
 }
 
 static int anyhit_brute(const oscene* sc, const double o[3], const double d[3], double tmax, ocount* cnt)
@@ -638,9 +689,7 @@ static int world_init(oworld* w, int64_t S, const double* sph, int64_t C, const 
 static void world_nearest(const oworld* w, const double o[3], const double d[3], double tmin, double tmax,
                           nearest_t* nr, ocount* cnt)
 {
-    nr->t1 = nr->t2 = INFINITY;
-    nr->id1 = nr->id2 = OR_MISS;
-    nr->t_graze = INFINITY;
+    nearest_reset(nr);
     if (w->mode == 1) nearest_grid(&w->sc, &w->gr, o, d, tmin, tmax, nr, cnt);
     else nearest_brute(&w->sc, o, d, tmin, tmax, nr, cnt);
 }
@@ -651,12 +700,33 @@ static int world_anyhit(const oworld* w, const double o[3], const double d[3], d
     return anyhit_brute(&w->sc, o, d, tmax, cnt);
 }
 
+/* Grazing ray (parity of hit ids is not asserted on it): a silhouette or
+ * clip-plane decision within rounding of flipping at or before the winning t
+ * (relative GRAZE_TIE), or a miss with such an encounter anywhere in front,
+ * or the two nearest distinct hits within a relative GRAZE_TIE. */
 static int is_grazing(const nearest_t* nr)
 {
     if (nr->id1 == OR_MISS) return nr->t_graze < INFINITY;
     if (nr->t_graze <= nr->t1 * (1.0 + GRAZE_TIE) + 1e-9) return 1;
     if (nr->id2 != OR_MISS && (nr->t2 - nr->t1) <= GRAZE_TIE * fabs(nr->t1)) return 1;
     return 0;
+}
+
+/* The other outcomes a grazing ray may legitimately give -- its runner-up
+ * (the second-nearest distinct hit) and the object of its nearest grazing
+ * encounter -- from the brute-force definition (the grid walk stops before
+ * the runner-up of a hit far ahead of it). Not counted as the method's work. */
+static void grazing_alternatives(const oworld* w, const double o[3], const double d[3], double tmin,
+                                 double tmax, nearest_t* nr)
+{
+    if (w->mode != 1) return;  /* brute force considered every object already */
+    nearest_t b;
+    ocount c = {0, 0, 0};
+    nearest_reset(&b);
+    nearest_brute(&w->sc, o, d, tmin, tmax, &b, &c);
+    nr->t2 = b.t2;
+    nr->id2 = b.id2;
+    nr->id_graze = b.id_graze;
 }
 
 int oracle_max_threads(void)
@@ -668,10 +738,14 @@ int oracle_max_threads(void)
 #endif
 }
 
-/* Nearest hits of explicit rays (o, d unit). out_grazing may be NULL. */
+/* Nearest hits of explicit rays (o, d unit). out_grazing, out_id2 and
+ * out_idg may be NULL; out_id2 / out_idg receive, for grazing rays, the
+ * runner-up and the object of the nearest grazing encounter (OR_MISS when
+ * there is none; OR_MISS on every other ray). */
 int oracle_nearest(int64_t S, const double* sph, int64_t C, const double* cyl, int32_t mode, double lambda,
                    int64_t nrays, const double* orig, const double* dirs, double tmin, double tmax,
-                   uint32_t* out_id, double* out_t, uint8_t* out_grazing, int64_t* counters)
+                   uint32_t* out_id, double* out_t, uint8_t* out_grazing, uint32_t* out_id2, uint32_t* out_idg,
+                   int64_t* counters)
 {
     oworld w;
     if (world_init(&w, S, sph, C, cyl, NULL, NULL, 0, mode, lambda)) return -1;
@@ -682,7 +756,11 @@ int oracle_nearest(int64_t S, const double* sph, int64_t C, const double* cyl, i
         world_nearest(&w, orig + 3 * r, dirs + 3 * r, tmin, tmax, &nr, &cnt);
         out_id[r] = nr.id1;
         out_t[r] = nr.id1 == OR_MISS ? INFINITY : nr.t1;
-        if (out_grazing) out_grazing[r] = (uint8_t)is_grazing(&nr);
+        const int gz = is_grazing(&nr);
+        if (gz) grazing_alternatives(&w, orig + 3 * r, dirs + 3 * r, tmin, tmax, &nr);
+        if (out_grazing) out_grazing[r] = (uint8_t)gz;
+        if (out_id2) out_id2[r] = gz ? nr.id2 : OR_MISS;
+        if (out_idg) out_idg[r] = gz ? nr.id_graze : OR_MISS;
         tot.cells += cnt.cells; tot.sph += cnt.sph; tot.cyl += cnt.cyl;
     }
     if (counters) { counters[0] = tot.cells; counters[1] = tot.sph; counters[2] = tot.cyl; }
@@ -768,7 +846,9 @@ int oracle_ao_probe(int64_t S, const double* sph, int64_t C, const double* cyl, 
  * raster, (m j + b) (m W) + (m i + a), which is the pixel index when m = 1.
  * Outputs (any may be NULL): rgb (3 doubles) per listed pixel; hit id
  * (0xFFFFFFFF = miss), hit t, number of unoccluded AO samples and grazing flag
- * per sub-sample, at [k m^2 + b m + a].
+ * per sub-sample, at [k m^2 + b m + a]; for grazing sub-samples the runner-up
+ * id and the id of the nearest grazing encounter (0xFFFFFFFF: none, and on
+ * every non-grazing sub-sample).
  * counters[16] (may be NULL): 0 primary rays, 1 AO rays, 2 hit pixels,
  *   3 primary cells, 4 primary sphere tests, 5 primary cylinder tests,
  *   6 AO cells, 7 AO sphere tests, 8 AO cylinder tests, 9 unoccluded AO rays.
@@ -781,7 +861,7 @@ int oracle_render(int64_t S, const double* sph, int64_t C, const double* cyl,
                   int32_t mode, double lambda,
                   int64_t npix, const int64_t* pix,
                   double* out_rgb, uint32_t* out_id, double* out_t, int32_t* out_vis, uint8_t* out_grazing,
-                  int64_t* counters, int32_t nthreads)
+                  uint32_t* out_id2, uint32_t* out_idg, int64_t* counters, int32_t nthreads)
 {
     if (W <= 0 || H <= 0) return -2;
     const int m = cam[15] >= 1.0 ? (int)cam[15] : 1;
@@ -851,7 +931,11 @@ int oracle_render(int64_t S, const double* sph, int64_t C, const double* cyl,
                     if (out_id) out_id[sub] = nr.id1;
                     if (out_t) out_t[sub] = nr.id1 == OR_MISS ? INFINITY : nr.t1;
                     if (out_vis) out_vis[sub] = vis;
-                    if (out_grazing) out_grazing[sub] = (uint8_t)is_grazing(&nr);
+                    const int gz = is_grazing(&nr);
+                    if (gz) grazing_alternatives(&w, o, d, 0.0, INFINITY, &nr);
+                    if (out_grazing) out_grazing[sub] = (uint8_t)gz;
+                    if (out_id2) out_id2[sub] = gz ? nr.id2 : OR_MISS;
+                    if (out_idg) out_idg[sub] = gz ? nr.id_graze : OR_MISS;
                 }
             }
             if (out_rgb) {

@@ -50,6 +50,25 @@ MUTANTS = {
                    "lit[l] = world_anyhit(&w, ao_o, ldir + 3 * l, INFINITY, &sc_);"),
     "shadow_flag": ("if (sp[11] != 0.0 && dot3(n, ldir + 3 * l) > 0.0)",
                     "if (sp[11] == 0.0 && dot3(n, ldir + 3 * l) > 0.0)"),
+    # the grazing classifier (which pixels hit-id parity is asserted on)
+    "graze_disc_big": ("#define GRAZE_DISC 1e-4", "#define GRAZE_DISC 1e-3"),
+    "graze_disc_small": ("#define GRAZE_DISC 1e-4", "#define GRAZE_DISC 1e-5"),
+    "graze_tie_big": ("#define GRAZE_TIE 1e-5", "#define GRAZE_TIE 1e-4"),
+    "graze_tie_small": ("#define GRAZE_TIE 1e-5", "#define GRAZE_TIE 1e-6"),
+    "graze_end_big": ("#define GRAZE_END 1e-4", "#define GRAZE_END 1e-3"),
+    "graze_tclose_sign": ("        g->t_close = -b;", "        g->t_close = b;"),
+    "graze_miss": ("if (nr->id1 == OR_MISS) return nr->t_graze < INFINITY;",
+                   "if (nr->id1 == OR_MISS) return 0;"),
+    "graze_before": ("if (nr->t_graze <= nr->t1 * (1.0 + GRAZE_TIE) + 1e-9) return 1;",
+                     "if (nr->t_graze < INFINITY) return 1;"),
+    "graze_tmin": ("fabs(g.disc_rel) < GRAZE_DISC && g.t_close > tmin &&", "fabs(g.disc_rel) < GRAZE_DISC &&"),
+    "graze_near_root": ("    if (g) g->t_near = t0;", ""),
+    "graze_far_root_end": ("        for (int k = 0; k < 2; ++k) {\n            if (g.end_mrg[k]",
+                           "        for (int k = 1; k < 2; ++k) {\n            if (g.end_mrg[k]"),
+    "graze_tube_segment": ("&& g.s_out <= GRAZE_END * (L + 1.0) &&", "&&"),
+    "graze_runner_up": ("    nr->id2 = b.id2;", "    nr->id2 = b.id1;"),
+    "graze_object": ("        nr->id_graze = (uint32_t)id;\n    }\n    if (id >= sc->S) {",
+                     "        nr->id_graze = OR_MISS;\n    }\n    if (id >= sc->S) {"),
 }
 
 
