@@ -13,7 +13,7 @@ import numpy as np
 import pytest
 
 from paper_0801_1500_gb300 import scenes as S
-from gpu_common import FRAC_OK, MAE_TOL, RGB_TOL
+from gpu_common import assert_ids, assert_rgb, id_stats
 
 pytestmark = pytest.mark.gpu
 
@@ -63,11 +63,8 @@ def render_aa(G, R, scene, grid, cam, W, H, lights, p):
 def check(rgb, ids, vis, ref, W, m, pixels, where):
     ids_o = fine_to_oracle(ids, W, m, pixels)
     vis_o = fine_to_oracle(vis, W, m, pixels)
-    ok = ~ref["grazing"]
-    assert int((ids_o[ok] != ref["id"][ok]).sum()) == 0, where
-    d = np.abs(rgb[pixels] - ref["rgb"])
-    assert float((d.max(axis=1) > RGB_TOL).mean()) <= 1.0 - FRAC_OK, (where, d.max())
-    assert float(d.mean()) <= MAE_TOL, (where, float(d.mean()))
+    assert_ids(*id_stats(ids_o, ref), len(ids_o), where)
+    assert_rgb(np.abs(rgb[pixels] - ref["rgb"]), where)
     return float((vis_o == ref["vis"].astype(np.uint32)).mean())
 
 

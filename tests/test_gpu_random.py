@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 from paper_0801_1500_gb300 import scenes as S
-from gpu_common import MAE_TOL, RGB_TOL
+from gpu_common import assert_ids, assert_rgb, id_stats
 
 pytestmark = pytest.mark.gpu
 
@@ -70,12 +70,8 @@ def test_random_configuration_vs_brute_force(G, R, oracle, k):
     fine_vis = vis.cpu().numpy().view(np.uint32).reshape(m * H, m * W)
     got_ids = fine_ids.reshape(H, m, W, m).transpose(0, 2, 1, 3).ravel()
     got_vis = fine_vis.reshape(H, m, W, m).transpose(0, 2, 1, 3).ravel()
-    ok = ~ref["grazing"]
-    assert int((got_ids[ok] != ref["id"][ok]).sum()) == 0, (k, W, H, m, p)
-    d = np.abs(rgb.cpu().numpy().reshape(-1, 3).astype(np.float64) - ref["rgb"])
-    bad = int((d.max(axis=1) > RGB_TOL).sum())
-    assert bad <= max(1, int(1e-3 * W * H)), (k, bad, float(d.max()))
-    assert float(d.mean()) <= MAE_TOL, (k, float(d.mean()))
+    assert_ids(*id_stats(got_ids, ref), len(got_ids), (k, W, H, m, p))
+    assert_rgb(np.abs(rgb.cpu().numpy().reshape(-1, 3).astype(np.float64) - ref["rgb"]), (k, W, H, m, p))
     if p.precision == S.PRECISION_FP64:
         assert float((got_vis == ref["vis"].astype(np.uint32)).mean()) >= 0.99, k
     R.free(scene, grid)

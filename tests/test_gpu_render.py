@@ -86,9 +86,7 @@ def test_ragged_frames(G, R, oracle, W, H, spp, prec):
     scene, grid = R.upload(sc, lam=1.0)
     rgb, ids, vis = gpu_frame(G, R, scene, grid, cam, W, H, S.default_lights(), p)
     ref = oracle.render(sc, cam, W, H, S.default_lights(), p, mode="brute")
-    st = compare(rgb, ids, vis, ref)
-    assert st["id_mismatch"] == 0, st
-    assert st["frac_bad"] <= max(1e-3, 1.0 / (W * H)), st
+    assert_parity(compare(rgb, ids, vis, ref), f"{W}x{H} spp {spp}")
     R.free(scene, grid)
 
 
@@ -130,14 +128,14 @@ def test_paper_scene_1mp_full_frame(G, R, oracle, paper, prec):
 
 
 def test_paper_scene_1mp_sampled_vs_brute_force(G, R, oracle, paper):
-    # sampled pixels against the brute-force definition (no grid on the oracle side)
+    # sampled pixels against the brute-force definition (no grid on the oracle
+    # side); 4,000 pixels, so the 99.9% rule allows 4 beyond 1/255
     w, scene, grid = paper
     p = S.Params(ao_samples=16, seed=0, precision=S.PRECISION_FP32)
     rgb, ids, vis = gpu_frame(G, R, scene, grid, w.camera, w.width, w.height, w.lights, p)
-    pix = np.random.default_rng(1).choice(w.width * w.height, 600, replace=False)
+    pix = np.random.default_rng(1).choice(w.width * w.height, 4000, replace=False)
     ref = oracle.render(w.scene, w.camera, w.width, w.height, w.lights, p, pixels=pix, mode="brute")
-    st = compare(rgb, ids, vis, ref, pixels=pix)
-    assert st["id_mismatch"] == 0 and st["frac_bad"] <= 1 / 300, st
+    assert_parity(compare(rgb, ids, vis, ref, pixels=pix), "paper 1mp vs brute force")
 
 
 def test_paper_scene_17mp_centre_crop(G, R, oracle, paper):
@@ -156,8 +154,7 @@ def test_paper_scene_17mp_centre_crop(G, R, oracle, paper):
     # sampled pixels over the whole frame
     pix = np.random.default_rng(2).choice(w2.width * w2.height, 4000, replace=False)
     ref = oracle.render(w2.scene, w2.camera, w2.width, w2.height, w2.lights, p, pixels=pix, mode="grid", lam=2.0)
-    st = compare(rgb, ids, vis, ref, pixels=pix)
-    assert st["id_mismatch"] == 0 and st["frac_bad"] <= 2e-3, st
+    assert_parity(compare(rgb, ids, vis, ref, pixels=pix), "17mp sampled")
 
 
 @pytest.mark.parametrize("prec", [S.PRECISION_FP32, S.PRECISION_FP64])
@@ -333,22 +330,27 @@ def test_asynchronous_host_outputs(G, R):
     R.free(scene, grid)
 
 
-def test_deterministic_and_grid_invariant(G, R):
+def test_deterministic_and_grid_invariant(G, R, oracle):
+    # the same frame twice is bit-identical; across grid densities the hit ids
+    # are identical on every non-grazing pixel (the result must not depend on
+    # the grid) and each frame meets the parity rule
     sc = S.globule(800, 760, 16.0, seed=5)
     W, H = 120, 90
     cam = S.ortho_camera(sc, W, H)
     p = S.Params(ao_samples=8, seed=1)
+    ref = oracle.render(sc, cam, W, H, S.default_lights(), p, mode="brute")
+    ok = ~ref["grazing"]
     frames = []
-    for lam in (0.5, 2.0, 8.0):
+    for lam in (0.25, 0.5, 1.0, 2.0, 8.0):
         scene, grid = R.upload(sc, lam=lam)
         a = gpu_frame(G, R, scene, grid, cam, W, H, S.default_lights(), p)
         b = gpu_frame(G, R, scene, grid, cam, W, H, S.default_lights(), p)
         assert all(np.array_equal(x, y) for x, y in zip(a, b))
+        assert_parity(compare(*a, ref), f"lambda {lam}")
         frames.append(a)
         R.free(scene, grid)
     for f in frames[1:]:
-        assert (f[1] != frames[0][1]).mean() < 1e-3
-        assert (np.abs(f[0] - frames[0][0]).max(axis=1) > 1 / 255).mean() < 2e-3
+        assert np.array_equal(f[1][ok], frames[0][1][ok])
 
 
 @pytest.mark.parametrize("prec", [S.PRECISION_FP32, S.PRECISION_FP64])
@@ -365,7 +367,8 @@ def test_open_tube_inner_wall(G, R, oracle, prec):
     hit = ref["id"] != oracle.MISS
     assert (ref["vis"][hit] < 16).sum() > 20  # the case under test occurs
     st = compare(rgb, ids, vis, ref)
-    assert st["id_mismatch"] == 0 and st["vis_eq"] >= 0.995, st
+    assert_parity(st, "open tube")
+    assert st["vis_eq"] >= 0.995, st
     R.free(scene, grid)
 
 
@@ -380,8 +383,7 @@ def test_pinhole_camera_inside_an_atom(G, R, oracle, prec):
     scene, grid = R.upload(sc, lam=2.0)
     rgb, ids, vis = gpu_frame(G, R, scene, grid, cam, W, H, S.default_lights(), p)
     ref = oracle.render(sc, cam, W, H, S.default_lights(), p, mode="brute")
-    st = compare(rgb, ids, vis, ref)
-    assert st["id_mismatch"] == 0 and st["frac_bad"] <= 1.0 / (W * H), st
+    assert_parity(compare(rgb, ids, vis, ref), "pinhole inside an atom")
     R.free(scene, grid)
 
 
