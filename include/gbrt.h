@@ -363,6 +363,17 @@ GBRT_API int gbrt_philox4x32_10(gbrt_ctx* ctx, const uint32_t* ctr, const uint32
  *    the call clears what must start at zero. Calls whose work overlaps on
  *    the GPU (different streams, or different host threads) race on it:
  *    order them on one stream.
+ *  - The scene and grid are read on `cuda_stream`, not on the stream of the
+ *    context that made them. After gbrt_scene_update or gbrt_grid_rebuild
+ *    (asynchronous on the context's stream) the caller must order
+ *    `cuda_stream` after that stream -- gbrt_sync on the context, or an event
+ *    recorded there that `cuda_stream` waits on -- before this call, else it
+ *    may read half-written geometry or cells.
+ *  - The set-up is kept for the life of the process: after a reset of the
+ *    device (cudaDeviceReset) the library must not be used again.
+ *  - A CUDA error already pending in the calling thread (from the caller's
+ *    earlier work) makes the call return GBRT_EDEVICE with nothing enqueued;
+ *    the error stays pending for the caller.
  *  - Arguments as for gbrt_render; output buffers are caller-owned.
  *    Asynchronous on `cuda_stream`. Device-side walk-bound errors are not
  *    reported by this entry point. */

@@ -87,6 +87,10 @@ extern "C" GBRT_API int gbrt_render_noalloc(const gbrt_scene* scene, const gbrt_
     if (params->out_flags != 0) return GBRT_EINVAL;  // outputs must be device memory
     if ((int64_t)width * height > GBRT_NOALLOC_MAX_PIXELS) return GBRT_EINVAL;
     if (camera->aa > 1) return GBRT_EINVAL;  // supersampling needs a finer-raster buffer
+    // an error left pending by the caller's earlier work is the caller's:
+    // report it without enqueueing anything and leave it pending, so the
+    // error read after this call's own launch below is this call's
+    if (cudaPeekAtLastError() != cudaSuccess) return GBRT_EDEVICE;
     int prev = -1;
     if (cudaGetDevice(&prev) != cudaSuccess) return GBRT_EDEVICE;
     if (prev != scene->device && cudaSetDevice(scene->device) != cudaSuccess) return GBRT_EDEVICE;

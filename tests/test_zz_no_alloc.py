@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 from paper_0801_1500_gb300 import scenes as S
-from gpu_common import compare
+from gpu_common import assert_parity, compare
 
 pytestmark = pytest.mark.gpu
 
@@ -86,3 +86,82 @@ def test_noalloc_rejects_supersampling(G):
         with pytest.raises(G.GbrtError) as e:
             G.gbrt_render_noalloc(scene, grid, cam, W, H, 4, S.default_lights(), S.Params(), out)
         assert e.value.code == G.EINVAL
+
+
+def test_noalloc_allocates_nothing_and_matches_the_oracle(G, oracle):
+    # after one call of each precision (the set-up, and the first launch of
+    # each kernel), twenty calls of mixed size and precision change neither
+    # torch's allocations nor the device's free memory; one of the frames is
+    # checked against the FP64 oracle directly
+    import torch
+    sc = S.globule(600, 570, 15.0, seed=7)
+    lights = S.default_lights()
+    sizes = [(256, 256), (97, 61), (1, 1), (200, 120), (17, 301)]
+    precs = [S.PRECISION_FP32, S.PRECISION_FP64]
+    with G.Renderer(0) as r:
+        scene, grid = r.upload(sc, lam=2.0)
+        stream = torch.cuda.current_stream()
+        outs = {}
+        for W, H in sizes:
+            for prec in precs:
+                dt = torch.float64 if prec == S.PRECISION_FP64 else torch.float32
+                outs[W, H, prec] = (torch.empty((H, W, 3), dtype=dt, device="cuda"),
+                                    torch.empty((H, W), dtype=torch.int32, device="cuda"),
+                                    torch.empty((H, W), dtype=torch.int32, device="cuda"))
+
+        def call(k, W, H, prec):
+            p = S.Params(ao_samples=3 + k % 6, seed=k, frame=k, precision=prec, shadows=bool(k % 3 == 0))
+            cam = S.ortho_camera(sc, W, H, angle_deg=13.0 * k)
+            G.gbrt_render_noalloc(scene, grid, cam, W, H, p.ao_samples, lights, p, *outs[W, H, prec], stream=stream)
+            return cam, p
+
+        for k, prec in enumerate(precs):
+            call(3 * k, *sizes[0], prec)   # shadows on: every kernel of the path runs once per precision
+        torch.cuda.synchronize()
+        free0, alloc0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
+        last = None
+        for k in range(20):
+            W, H = sizes[k % len(sizes)]
+            prec = precs[(k // len(sizes)) % 2]
+            last = (W, H, prec) + call(k, W, H, prec)
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
+        assert torch.cuda.memory_allocated() == alloc0
+        W, H, prec, cam, p = last
+        rgb, ids, vis = outs[W, H, prec]
+        ref = oracle.render(sc, cam, W, H, lights, p, mode="brute")
+        st = compare(rgb.cpu().numpy().reshape(-1, 3).astype(np.float64), ids.cpu().numpy().view(np.uint32).ravel(),
+                     vis.cpu().numpy().view(np.uint32).ravel(), ref)
+        assert_parity(st, "noalloc vs oracle")
+        r.free(scene, grid)
+
+
+def test_noalloc_after_update_and_rebuild_ordered_by_an_event(G):
+    # the scene and grid change on the context's stream; the caller's stream
+    # waits on an event recorded there, then renders without allocating: the
+    # same frame as gbrt_render on the context
+    import torch
+    base = S.globule(800, 760, 16.0, seed=5)
+    traj = S.MDTrajectory(base, amplitude=0.3, spin_deg=5.0, seed=2)
+    W, H = 90, 70
+    lights = S.default_lights()
+    p = S.Params(ao_samples=5, seed=1)
+    ctx_stream = torch.cuda.Stream()
+    caller = torch.cuda.Stream()
+    with G.Renderer(0, ctx_stream) as r:
+        scene, grid = r.upload(base, lam=2.0)
+        cam = S.ortho_camera(base, W, H)
+        for k in range(1, 4):
+            fr = traj.frame(k)
+            G.gbrt_scene_update(r.ctx, scene, fr.spheres, fr.cylinders)
+            G.gbrt_grid_rebuild(r.ctx, grid, scene)
+            ev = torch.cuda.Event()
+            ev.record(ctx_stream)
+            caller.wait_event(ev)
+            got = (torch.empty((H, W, 3), device="cuda"), torch.empty((H, W), dtype=torch.int32, device="cuda"))
+            G.gbrt_render_noalloc(scene, grid, cam, W, H, 5, lights, p, *got, stream=caller)
+            caller.synchronize()
+            ref = r.render(scene, grid, cam, W, H, lights, p, ids=True)
+            G.gbrt_sync(r.ctx)
+            assert torch.equal(ref[0], got[0]) and torch.equal(ref[1], got[1]), k
+        r.free(scene, grid)
