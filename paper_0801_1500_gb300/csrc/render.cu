@@ -305,6 +305,71 @@ __global__ void k_ao_plan(const __grid_constant__ BatchDev b) {
 
 // ---------------------------------------------------------------- AO pass
 
+// One AO job -- AO sample or direct-light shadow ray -- of the batch's
+// global job index jj (hits of all frames x jobs per hit): the hit slot whose
+// count or light bit it settles, its ray, and the hit's own object when that
+// object cannot be met again (a hit on a convex outer side), else GBRT_MISS.
+template <class R>
+struct AoJob {
+    V3<R> o, d;
+    R tmax;
+    uint32_t lbit;  // 0: an AO sample; 1 << l: the shadow ray toward light l
+    uint32_t self;
+    int64_t vslot;
+    const FrameDev* F;
+};
+
+// False when no ray is cast: the surface faces away from the light (its bit
+// stays clear).
+template <class R>
+__device__ __forceinline__ bool ao_job(const BatchDev& b, unsigned long long jj, AoJob<R>& J) {
+    const int f = find_frame(b.job_off, b.nframes, jj);
+    const FrameDev& F = b.frames[f];
+    J.F = &F;
+    const unsigned long long jl = jj - b.job_off[f];
+    const uint32_t jph = (uint32_t)F.jobs_per_hit;
+    uint32_t h;
+    if (jl >= 0xFFFFFFFFull) {
+        h = (uint32_t)(jl / jph);
+    } else if (jph > 1u) {
+        // jl / jph by the multiplier ceil(2^32 / jph): the product's high word
+        // is the quotient or one more
+        h = __umulhi((uint32_t)jl, F.jph_magic);
+        if ((unsigned long long)h * jph > jl) --h;
+    } else {
+        h = (uint32_t)jl;
+    }
+    const uint32_t smp = (uint32_t)(jl - (unsigned long long)h * jph);
+    J.vslot = F.hit_base + h;
+    V3<R> n;
+    uint32_t q;
+    HitIO<R>::load(b.hits, J.vslot, J.o, n, q, J.self);
+    // the own object can be skipped only behind a convex outer side
+    if (q & HIT_INSIDE) J.self = GBRT_MISS;
+    q &= ~HIT_INSIDE;
+    if (smp < (uint32_t)F.spp) {
+        uint32_t b1, b2;
+        ao_uniforms(q, smp, F.frame, F.seed_lo, F.seed_hi, b1, b2);
+        J.d = cosine_dir(n, b1, b2);
+        J.tmax = ao_maxdist<R>(F);
+        J.lbit = 0u;
+        return true;
+    }
+    // shadow ray toward light l (none where the surface faces away)
+    const int l = (int)(smp - (uint32_t)F.spp);
+    J.d = ShadeP<R>::ldir(F, l);
+    J.tmax = Num<R>::inf();
+    J.lbit = 1u << l;
+    return dot(n, J.d) > R(0);
+}
+
+// A ray that leaves the objects' bounds unoccluded: one more escaped AO
+// sample, or its light's bit.
+__device__ __forceinline__ void ao_escape(const BatchDev& b, int64_t vslot, uint32_t lbit) {
+    if (lbit) atomicOr(b.lmask + vslot, lbit);
+    else atomicAdd(b.vis + vslot, 1u);
+}
+
 // Ray record in shared memory: (origin, tmax) and (direction, -) -- two
 // 128-bit loads per test in the FP32 path.
 template <class R>
@@ -336,16 +401,19 @@ constexpr unsigned AO_MIN_PAIRS = 6;
 // AO rays a warp claims from the global queue at once (its local pool)
 constexpr unsigned AO_CLAIM = 64;
 
-// Per-precision choices. FP32: a 4-slot mailbox and pairs tested where they
-// were mapped, which keeps the walk's shared state at 4 KB a warp (below).
-// FP64: the test occupies the FP64 pipe, so lanes left idle cost more than
-// shared memory -- an 8-slot mailbox, and surviving pairs queued and tested
-// in full batches of 32 (in-place tests measured 13% slower there).
+// Per-precision choices. FP32: pairs are tested where they were mapped, one
+// per lane, so a lane whose pair is a re-test would compute and discard it
+// anyway -- no mailbox (a re-test of a missed object misses again, and the
+// hit's own object cannot be met behind a convex outer side, so testing
+// either is exact). FP64: the test occupies the FP64 pipe, so lanes left idle
+// cost more than shared memory -- an 8-slot mailbox drops re-tests, and the
+// surviving pairs are queued and tested in full batches of 32 (in-place tests
+// measured 13% slower there).
 template <class R>
 struct AoCfg;
 template <>
 struct AoCfg<float> {
-    static constexpr int mbox = 4;
+    static constexpr int mbox = 0;
     static constexpr bool queue = false;
 };
 template <>
@@ -361,50 +429,89 @@ struct AoQueue<R, true> {
     uint2 q[64];  // queued pairs (ray lane, object id)
 };
 
-// 4 KB a warp in the FP32 path: four resident CTAs of 8 warps fit the 132 KB
-// shared-memory configuration, leaving 124 KB of the SM's 256 KB to the L1
-// that caches the walk's cell, item and object loads. Measured: 5.25 KB a
-// warp (60 KB of L1) 2.5% slower, 5 KB (92 KB of L1, with an 8-slot mailbox
-// and a test queue) 1% slower.
+// per ray: direct-mapped ids it already tested (rows padded by one word so
+// distinct rays and slots fall in distinct banks)
+template <class R, int M = AoCfg<R>::mbox>
+struct AoMbox {
+    uint32_t mbox[32][M + 1];
+};
 template <class R>
-struct AoWarp : AoQueue<R> {
-    AoRay<R> ray[32];
-    // item index of pair p of ray r: p + sd[g][r].y for the last cell g whose
-    // pairs start at or before p (sd[g][r].x)
-    uint2 sd[AO_CELLS][32];
-    uint32_t owner[32];  // ray whose pairs start at this position of the current chunk
-    uint32_t mbox[32][AoCfg<R>::mbox + 1];
+struct AoMbox<R, 0> {};
+
+// per ray: its scene records and grid item list, when a batch mixes scenes
+// (UNI: every frame of the batch has the same scene and grid -- the pointers
+// are then kernel-wide)
+template <class R, bool UNI>
+struct AoPtrs {
     ObjPtr<R> obj[32];
     const uint32_t* items[32];
+};
+template <class R>
+struct AoPtrs<R, true> {};
+
+// 4 KB a warp at most in the FP32 path: four resident CTAs of 8 warps fit the
+// 132 KB shared-memory configuration, leaving 124 KB of the SM's 256 KB to the
+// L1 that caches the walk's cell, item and object loads. Measured: 5.25 KB a
+// warp (60 KB of L1) 2.5% slower, 5 KB (92 KB of L1, with an 8-slot mailbox
+// and a test queue) 1% slower.
+static_assert(AO_CELLS == 4, "the pair segments of a ray are kept as one uint4 of starts and one of offsets");
+template <class R, bool UNI>
+struct AoWarp : AoQueue<R>, AoMbox<R>, AoPtrs<R, UNI> {
+    AoRay<R> ray[32];
+    // item index of pair p of ray r: p + sdo[r][g] for the last cell g whose
+    // pairs start at or before p (sds[r][g])
+    uint4 sds[32];
+    uint4 sdo[32];
+    uint32_t owner[32];  // ray whose pairs start at this position of the current chunk
     // cells a ray has loaded but not yet taken, oldest first: an iteration takes
     // at least one of its at most AO_CELLS cells, so AO_CELLS - 1 wait at most
     uint2 fifo[32][AO_CELLS - 1];
 };
-static_assert(sizeof(AoWarp<float>) <= 4096, "the FP32 AO walk's per-warp state outgrew its 4 KB");
+static_assert(sizeof(AoWarp<float, false>) <= 4096, "the FP32 AO walk's per-warp state outgrew its 4 KB");
+
+template <class R, bool UNI>
+__device__ __forceinline__ ObjPtr<R> ao_obj(const AoWarp<R, UNI>& S, unsigned r, ObjPtr<R> uni) {
+    if constexpr (UNI) return uni;
+    else return S.obj[r];
+}
+template <class R, bool UNI>
+__device__ __forceinline__ const uint32_t* ao_items(const AoWarp<R, UNI>& S, unsigned r, const uint32_t* uni) {
+    if constexpr (UNI) return uni;
+    else return S.items[r];
+}
 
 // FP64 path: test queued pairs [0, n) (1 <= n <= 32), one per lane (lanes
 // past n redo pair 0 and discard it, so the batch runs without branches);
 // returns the rays hit, as bits.
-template <class R>
-__device__ __forceinline__ unsigned ao_test_batch(AoWarp<R>& S, int lane, unsigned n) {
+template <class R, bool UNI>
+__device__ __forceinline__ unsigned ao_test_batch(AoWarp<R, UNI>& S, int lane, unsigned n, ObjPtr<R> uobj) {
     const unsigned idx = (unsigned)lane < n ? (unsigned)lane : 0u;
     const uint2 e = S.q[idx];
     const unsigned r = e.x;
     const uint32_t id = e.y;
     const AoRay<R> ray = S.ray[r];
     R t;
-    const bool hit = hit_object<R>(S.obj[r], id, ray.o, ray.d, R(0), ray.tmax, t) && (unsigned)lane < n;
+    const bool hit = hit_object<R>(ao_obj(S, r, uobj), id, ray.o, ray.d, R(0), ray.tmax, t) && (unsigned)lane < n;
     return __reduce_or_sync(FULL, hit ? (1u << r) : 0u);
 }
 
 // Lockstep cooperative walk: every iteration each active ray takes its next
 // one to AO_CELLS cells (all lanes run the same step code); the warp lays the
 // (ray, item) pairs of those cells out densely with a scan and tests them 32
-// at a time, one pair per lane, skipping the ray's own object and re-tests.
-template <class R>
+// at a time, one pair per lane (the FP64 path skipping the ray's own object
+// and re-tests). UNI: every frame of the batch has the same scene and grid.
+template <class R, bool UNI>
 __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDev b) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    AoWarp<R>& S = reinterpret_cast<AoWarp<R>*>(smem_raw)[threadIdx.x >> 5];
+    AoWarp<R, UNI>& S = reinterpret_cast<AoWarp<R, UNI>*>(smem_raw)[threadIdx.x >> 5];
+    ObjPtr<R> uobj = nullptr;
+    const uint32_t* uitems = nullptr;
+    const uint2* ucells = nullptr;
+    if constexpr (UNI) {
+        uobj = Obj<R>::base(b.frames[0].scene);
+        uitems = b.frames[0].grid.items;
+        ucells = b.frames[0].grid.cells;
+    }
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     const unsigned long long total = b.job_off[b.nframes];
@@ -437,72 +544,40 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
                 const unsigned i = __popc(idle & lt);
                 const unsigned long long jj = i < rem ? pool + i : fresh_base + (i - rem);
                 if (jj < total) {
-                    const int f = find_frame(b.job_off, b.nframes, jj);
-                    const FrameDev& F = b.frames[f];
-                    const unsigned long long jl = jj - b.job_off[f];
-                    const uint32_t jph = (uint32_t)F.jobs_per_hit;
-                    uint32_t h;
-                    if (jl >= 0xFFFFFFFFull) {
-                        h = (uint32_t)(jl / jph);
-                    } else if (jph > 1u) {
-                        // jl / jph by the multiplier ceil(2^32 / jph): the product's
-                        // high word is the quotient or one more
-                        h = __umulhi((uint32_t)jl, F.jph_magic);
-                        if ((unsigned long long)h * jph > jl) --h;
-                    } else {
-                        h = (uint32_t)jl;
-                    }
-                    const uint32_t smp = (uint32_t)(jl - (unsigned long long)h * jph);
-                    vslot = F.hit_base + h;
-                    V3<R> o, n;
-                    uint32_t q, self;
-                    HitIO<R>::load(b.hits, vslot, o, n, q, self);
-                    // the own object can be skipped only behind a convex outer side
-                    if (q & HIT_INSIDE) self = GBRT_MISS;
-                    q &= ~HIT_INSIDE;
-                    V3<R> d;
-                    R tmax;
-                    bool cast = true;
-                    if (smp < (uint32_t)F.spp) {
-                        uint32_t b1, b2;
-                        ao_uniforms(q, smp, F.frame, F.seed_lo, F.seed_hi, b1, b2);
-                        d = cosine_dir(n, b1, b2);
-                        tmax = ao_maxdist<R>(F);
-                        lbit = 0u;
-                    } else {
-                        // shadow ray toward light l (none where the surface faces away)
-                        const int l = (int)(smp - (uint32_t)F.spp);
-                        d = ShadeP<R>::ldir(F, l);
-                        tmax = Num<R>::inf();
-                        lbit = 1u << l;
-                        cast = dot(n, d) > R(0);
-                    }
+                    AoJob<R> J;
+                    const bool cast = ao_job<R>(b, jj, J);
+                    vslot = J.vslot;
+                    lbit = J.lbit;
                     if (!cast) {
                         // the light cannot reach this side: its bit stays clear
-                    } else if (walk_start(F.grid, o, d, R(0), tmax, w)) {
-                        cells = F.grid.cells;
+                    } else if (walk_start(J.F->grid, J.o, J.d, R(0), J.tmax, w)) {
+                        if constexpr (UNI) {
+                            cells = ucells;
+                        } else {
+                            cells = J.F->grid.cells;
+                            S.obj[lane] = Obj<R>::base(J.F->scene);
+                            S.items[lane] = J.F->grid.items;
+                        }
                         AoRay<R> ray;
-                        ray.o = o;
-                        ray.tmax = tmax;
-                        ray.d = d;
+                        ray.o = J.o;
+                        ray.tmax = J.tmax;
+                        ray.d = J.d;
                         ray.pad = R(0);
                         S.ray[lane] = ray;
-                        S.obj[lane] = Obj<R>::base(F.scene);
-                        S.items[lane] = F.grid.items;
+                        if constexpr (AoCfg<R>::mbox > 0) {
 #pragma unroll
-                        for (int m = 0; m < AoCfg<R>::mbox; ++m) S.mbox[lane][m] = GBRT_MISS;
-                        // the own object starts in the mailbox: it is skipped like a
-                        // re-test while it stays there (testing it is harmless too --
-                        // behind a convex outer side the ray cannot meet it again)
-                        if (self != GBRT_MISS) S.mbox[lane][self & (AoCfg<R>::mbox - 1)] = self;
+                            for (int m = 0; m < AoCfg<R>::mbox; ++m) S.mbox[lane][m] = GBRT_MISS;
+                            // the own object starts in the mailbox: it is skipped like a
+                            // re-test while it stays there (testing it is harmless too --
+                            // behind a convex outer side the ray cannot meet it again)
+                            if (J.self != GBRT_MISS) S.mbox[lane][J.self & (AoCfg<R>::mbox - 1)] = J.self;
+                        }
                         nf = 0;
                         wend = false;
                         has = true;
                         fresh = true;  // the walk stands on its first cell, not yet loaded
-                    } else if (lbit) {
-                        atomicOr(b.lmask + vslot, lbit);  // misses the objects' bounds: escapes
                     } else {
-                        atomicAdd(b.vis + vslot, 1u);
+                        ao_escape(b, vslot, lbit);  // misses the objects' bounds: escapes
                     }
                 }
             }
@@ -585,17 +660,13 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
         unsigned hitbits = 0;
         if (T > 0) {
             const unsigned ex = incl - cnt;
-            unsigned run = ex;
-#pragma unroll
-            for (int g = 0; g < AO_CELLS; ++g) {
-                S.sd[g][lane] = make_uint2(run, kg[g] - run);
-                run += ng[g];
-            }
-            // 4. map pairs to (ray, object) 32 at a time, skip the own object
-            //    and re-tests, and test the rest: in place in the FP32 path
-            //    (the skipped pairs' lanes compute and discard, so the test runs
-            //    without branches), through the queue in full batches of 32 in
-            //    the FP64 path
+            const unsigned s1 = ex + ng[0], s2 = s1 + ng[1], s3 = s2 + ng[2];
+            S.sds[lane] = make_uint4(ex, s1, s2, s3);
+            S.sdo[lane] = make_uint4(kg[0] - ex, kg[1] - s1, kg[2] - s2, kg[3] - s3);
+            // 4. map pairs to (ray, object) 32 at a time and test them: in
+            //    place in the FP32 path (lanes past the last pair redo it, so
+            //    the test runs without branches), through the queue in full
+            //    batches of 32 after the mailbox in the FP64 path
             unsigned qn = 0;
             for (unsigned base = 0; base < T; base += 32) {
                 // rays mark where their pairs start inside this chunk; a pair's
@@ -607,17 +678,15 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
                 __syncwarp();
                 const unsigned p = base + lane < T ? base + lane : T - 1u;
                 const unsigned r = S.owner[31 - __clz(starts & (0xFFFFFFFFu >> (31 - lane)))];
-                unsigned di = S.sd[0][r].y;
-#pragma unroll
-                for (int g = 1; g < AO_CELLS; ++g) {
-                    const uint2 e = S.sd[g][r];
-                    if (p >= e.x) di = e.y;
-                }
-                const uint32_t id = __ldg(S.items[r] + (p + di));
-                uint32_t* slot = &S.mbox[r][id & (AoCfg<R>::mbox - 1)];
-                const uint32_t seen = *slot;
-                const bool keep = base + lane < T && seen != id;
+                const uint4 st = S.sds[r], so = S.sdo[r];
+                unsigned di = so.x;
+                di = p >= st.y ? so.y : di;
+                di = p >= st.z ? so.z : di;
+                di = p >= st.w ? so.w : di;
+                const uint32_t id = __ldg(ao_items(S, r, uitems) + (p + di));
                 if constexpr (AoCfg<R>::queue) {
+                    uint32_t* slot = &S.mbox[r][id & (AoCfg<R>::mbox - 1)];
+                    const bool keep = base + lane < T && *slot != id;
                     const unsigned bal = __ballot_sync(FULL, keep);
                     if (keep) {
                         *slot = id;
@@ -626,23 +695,22 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
                     qn += __popc(bal);
                     __syncwarp();
                     if (qn >= 32) {
-                        hitbits |= ao_test_batch(S, lane, 32u);
+                        hitbits |= ao_test_batch(S, lane, 32u, uobj);
                         __syncwarp();
                         if ((unsigned)lane < qn - 32) S.q[lane] = S.q[32 + lane];
                         qn -= 32;
                         __syncwarp();
                     }
                 } else {
-                    if (keep) *slot = id;
                     const AoRay<R> ray = S.ray[r];
                     R t;
-                    const bool hit = hit_object<R>(S.obj[r], id, ray.o, ray.d, R(0), ray.tmax, t) && keep;
+                    const bool hit = hit_object<R>(ao_obj(S, r, uobj), id, ray.o, ray.d, R(0), ray.tmax, t);
                     hitbits |= __reduce_or_sync(FULL, hit ? (1u << r) : 0u);
                     __syncwarp();
                 }
             }
             if constexpr (AoCfg<R>::queue) {
-                if (qn > 0) hitbits |= ao_test_batch(S, lane, qn);
+                if (qn > 0) hitbits |= ao_test_batch(S, lane, qn, uobj);
             }
         }
         // 5. any hit occludes the ray; a ray whose walk ended escapes
@@ -805,31 +873,75 @@ struct Grids {
     int primary, ao, shade, resolve;
 };
 
-static Grids grids_for(Ctx* ctx, int precision) {
+// The AO walk of one precision and scene layout (UNI: one scene and grid for
+// the whole batch) with its dynamic shared memory; launched with an explicit
+// grid, or with one sized for the current device (grid <= 0).
+template <class R, bool UNI>
+static size_t ao_smem(int block) {
+    return (size_t)(block / 32) * sizeof(AoWarp<R, UNI>);
+}
+
+static cudaError_t set_ao_smem_limits() {
+    // the AO kernels' per-warp staging can exceed the 48 KB default
+    cudaError_t e = cudaFuncSetAttribute(k_ao_walk<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)ao_smem<float, false>(256));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_ao_walk<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)ao_smem<float, true>(256));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_ao_walk<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)ao_smem<double, false>(256));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_ao_walk<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)ao_smem<double, true>(256));
+    return e;
+}
+
+template <class R, bool UNI>
+static int ao_grid(Ctx* ctx, int block) {
+    return persistent_grid(ctx, k_ao_walk<R, UNI>, block, ao_smem<R, UNI>(block));
+}
+
+template <class R>
+static void launch_ao(const BatchDev& bd, bool uni, int grid, int block, cudaStream_t stream) {
+    if (uni) k_ao_walk<R, true><<<grid, block, ao_smem<R, true>(block), stream>>>(bd);
+    else k_ao_walk<R, false><<<grid, block, ao_smem<R, false>(block), stream>>>(bd);
+}
+
+static Grids grids_for(Ctx* ctx, int precision, bool uni) {
     const int block = ctx->tuning.block;
     if (!ctx->smem_configured) {
-        // the AO kernels' per-warp staging can exceed the 48 KB default
-        cudaFuncSetAttribute(k_ao_walk<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(8 * sizeof(AoWarp<float>)));
-        cudaFuncSetAttribute(k_ao_walk<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(8 * sizeof(AoWarp<double>)));
+        set_ao_smem_limits();
         ctx->smem_configured = true;
     }
     Grids g;
     if (precision == GBRT_FP32) {
         g.primary = persistent_grid(ctx, k_primary<GBRT_FP32>, block);
-        g.ao = persistent_grid(ctx, k_ao_walk<float>, block, (block / 32) * sizeof(AoWarp<float>));
+        g.ao = uni ? ao_grid<float, true>(ctx, block) : ao_grid<float, false>(ctx, block);
     } else {
         g.primary = persistent_grid(ctx, k_primary<GBRT_FP64>, block);
-        g.ao = persistent_grid(ctx, k_ao_walk<double>, block, (block / 32) * sizeof(AoWarp<double>));
+        g.ao = uni ? ao_grid<double, true>(ctx, block) : ao_grid<double, false>(ctx, block);
     }
     g.shade = ctx->num_sms * 8;
     g.resolve = ctx->num_sms * 4;
     return g;
 }
 
-// optional passes of a batch
-enum : int { EXTRA_RESOLVE = 1, EXTRA_PATCH = 2 };
+// Every frame of the batch reads the same scene and grid (device-side rebuilt
+// grids: the same rebuilt grid).
+static bool one_scene(const FrameDev* frames, int n) {
+    for (int f = 1; f < n; ++f) {
+        const FrameDev& a = frames[0];
+        const FrameDev& c = frames[f];
+        if (c.scene.obj != a.scene.obj || c.scene.obj64 != a.scene.obj64 || c.grid.items != a.grid.items ||
+            c.grid.cells != a.grid.cells || c.grid_src != a.grid_src)
+            return false;
+    }
+    return true;
+}
+
+// optional passes of a batch, and its scene layout
+enum : int { EXTRA_RESOLVE = 1, EXTRA_PATCH = 2, EXTRA_UNI = 4 };
 
 static int enqueue_batch(Ctx* ctx, cudaStream_t stream, int precision, const BatchDev& bd, size_t desc_bytes,
                          const Grids& gr, int extra) {
@@ -853,7 +965,7 @@ static int enqueue_batch(Ctx* ctx, cudaStream_t stream, int precision, const Bat
         mark(1);
         k_ao_plan<<<1, 32, 0, stream>>>(bd);
         mark(2);
-        k_ao_walk<float><<<gr.ao, block, (block / 32) * sizeof(AoWarp<float>), stream>>>(bd);
+        launch_ao<float>(bd, (extra & EXTRA_UNI) != 0, gr.ao, block, stream);
         mark(3);
         k_shade<float><<<gr.shade, 256, 0, stream>>>(bd);
         if (resolve) k_resolve<float><<<dim3(gr.resolve, std::min(bd.nframes, 65535)), 256, 0, stream>>>(bd);
@@ -862,7 +974,7 @@ static int enqueue_batch(Ctx* ctx, cudaStream_t stream, int precision, const Bat
         mark(1);
         k_ao_plan<<<1, 32, 0, stream>>>(bd);
         mark(2);
-        k_ao_walk<double><<<gr.ao, block, (block / 32) * sizeof(AoWarp<double>), stream>>>(bd);
+        launch_ao<double>(bd, (extra & EXTRA_UNI) != 0, gr.ao, block, stream);
         mark(3);
         k_shade<double><<<gr.shade, 256, 0, stream>>>(bd);
         if (resolve) k_resolve<double><<<dim3(gr.resolve, std::min(bd.nframes, 65535)), 256, 0, stream>>>(bd);
@@ -956,7 +1068,9 @@ int render_frames(Ctx* ctx, FrameDev* frames, int n, bool use_graph) {
     bd.refill = ctx->tuning.refill;
     ctx->counters_bytes_used = counters_bytes;
 
-    const Grids gr = grids_for(ctx, precision);
+    const bool uni = one_scene(frames, n);
+    if (uni) extra |= EXTRA_UNI;
+    const Grids gr = grids_for(ctx, precision, uni);
     if (!use_graph) {
         rc = enqueue_batch(ctx, ctx->stream, precision, bd, desc_bytes, gr, extra);
     } else {
@@ -997,14 +1111,7 @@ int render_frames(Ctx* ctx, FrameDev* frames, int n, bool use_graph) {
     return GBRT_OK;
 }
 
-int configure_render_kernels() {
-    cudaError_t e = cudaFuncSetAttribute(k_ao_walk<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(8 * sizeof(AoWarp<float>)));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_ao_walk<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(8 * sizeof(AoWarp<double>)));
-    return err_of(e);
-}
+int configure_render_kernels() { return err_of(set_ao_smem_limits()); }
 
 int enqueue_prepared(const BatchDev& bd, int precision, cudaStream_t stream, int block, int num_sms, bool patch) {
     auto grid_of = [&](auto kernel, size_t smem) {
@@ -1013,18 +1120,17 @@ int enqueue_prepared(const BatchDev& bd, int precision, cudaStream_t stream, int
             per_sm = 1;
         return per_sm * num_sms;
     };
+    // one frame: one scene and grid
     if (patch) k_patch_grids<<<1, 128, 0, stream>>>(bd);
     if (precision == GBRT_FP32) {
-        const size_t smem = (block / 32) * sizeof(AoWarp<float>);
         k_primary<GBRT_FP32><<<grid_of(k_primary<GBRT_FP32>, 0), block, 0, stream>>>(bd);
         k_ao_plan<<<1, 32, 0, stream>>>(bd);
-        k_ao_walk<float><<<grid_of(k_ao_walk<float>, smem), block, smem, stream>>>(bd);
+        launch_ao<float>(bd, true, grid_of(k_ao_walk<float, true>, ao_smem<float, true>(block)), block, stream);
         k_shade<float><<<num_sms * 8, 256, 0, stream>>>(bd);
     } else {
-        const size_t smem = (block / 32) * sizeof(AoWarp<double>);
         k_primary<GBRT_FP64><<<grid_of(k_primary<GBRT_FP64>, 0), block, 0, stream>>>(bd);
         k_ao_plan<<<1, 32, 0, stream>>>(bd);
-        k_ao_walk<double><<<grid_of(k_ao_walk<double>, smem), block, smem, stream>>>(bd);
+        launch_ao<double>(bd, true, grid_of(k_ao_walk<double, true>, ao_smem<double, true>(block)), block, stream);
         k_shade<double><<<num_sms * 8, 256, 0, stream>>>(bd);
     }
     return err_of(cudaGetLastError());
