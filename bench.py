@@ -36,10 +36,13 @@ sys.path.insert(0, ROOT)
 
 from paper_0801_1500_gb300 import scenes as S  # noqa: E402
 
-# FP32 flops of one step of each kind, counted from the formulas of the device
-# code (an FMA counts 2, sqrt / reciprocal 1): grid-walk step, ray-sphere test,
-# ray-cylinder test.
-FLOPS_CELL, FLOPS_SPHERE, FLOPS_CYLINDER = 8, 24, 58
+# Algorithmic flops of one step of each kind, the roofline's fixed convention
+# (an FMA counts 2, a square root or reciprocal 1): grid-walk step 8,
+# ray-sphere test 20 (the sphere's own formula), ray-cylinder test 50.
+FLOPS_CELL, FLOPS_SPHERE, FLOPS_CYLINDER = 8, 20, 50
+# The same counts taken from the device code's one branch-free test, which
+# runs the cylinder formula for spheres too (reported beside the roofline).
+FLOPS_SPHERE_DEVICE, FLOPS_CYLINDER_DEVICE = 24, 58
 # bytes a walk reads per step: a cell record (8 B), an item id (4 B), a sphere
 # record (16 B) or a cylinder record (32 B)
 BYTES_CELL, BYTES_ITEM, BYTES_SPHERE, BYTES_CYLINDER = 8, 4, 16, 32
@@ -219,14 +222,15 @@ def oracle_sample(w, lam, budget_s=15.0, threads=0):
                 cores=oracle.max_threads() if threads <= 0 else threads)
 
 
-def per_ray_work(c, kind="ao"):
-    """Algorithmic FP32 flops and walk bytes per ray (of one kind: "ao" or
+def per_ray_work(c, kind="ao", device_formulas=False):
+    """Algorithmic flops and walk bytes per ray (of one kind: "ao" or
     "primary") from the oracle's grid-walk counters."""
     rays = max(1, c[f"{kind}_rays"])
     cells = c[f"{kind}_cells"]
     sph = c[f"{kind}_sphere_tests"]
     cyl = c[f"{kind}_cylinder_tests"]
-    flops = (cells * FLOPS_CELL + sph * FLOPS_SPHERE + cyl * FLOPS_CYLINDER) / rays
+    fs, fc = (FLOPS_SPHERE_DEVICE, FLOPS_CYLINDER_DEVICE) if device_formulas else (FLOPS_SPHERE, FLOPS_CYLINDER)
+    flops = (cells * FLOPS_CELL + sph * fs + cyl * fc) / rays
     nbytes = (cells * BYTES_CELL + (sph + cyl) * BYTES_ITEM + sph * BYTES_SPHERE + cyl * BYTES_CYLINDER) / rays
     return flops, nbytes
 
@@ -372,6 +376,40 @@ def replay(srv, SV, reqs_spec, scenes, precision):
             "p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 2),
             "max_ms": round(float(lat.max()) * 1e3, 2), "wall_s": round(t1 - t0, 3),
             "Mrays_s": round(rays / (t1 - t0) / 1e6, 1), "waves": srv.stats()["waves"]}
+
+
+def serving_extra(args, local, paper_scene, stream_s=3.0, trace_s=1.0, rate=200.0):
+    """Bounded serving figures for the default run: the paper-sized scene at
+    965x1137, 16 spp streamed at 30 requests/s for stream_s seconds; then
+    trace_s seconds of the Poisson trace at `rate` requests/s over the 8
+    serving scenes (it offers far more rays than one GPU renders, so the
+    queue grows and the latencies include the wait)."""
+    from paper_0801_1500_gb300 import serve as SV
+    lam = args.lam or 8.0
+    out = {}
+    be = SV.GpuBackend(local, lam=lam)
+    srv = SV.Server(be, [paper_scene], hbm_budget=int(args.hbm_gb * (1 << 30)), wave_rays=24e6, band_rows=1137)
+    n = int(round(30.0 * stream_s))
+    trace = [dict(id=k, arrival_s=k / 30.0, scene=0, width=965, height=1137, spp=16, angle_deg=0.0) for k in range(n)]
+    res = replay(srv, SV, trace, [paper_scene], S.PRECISION_FP32)
+    srv.close()
+    be.close()
+    # a throttled stream: it is sustained when every frame is done within a
+    # frame interval of its arrival
+    res["offered_fps"] = 30.0
+    res["sustained"] = res["completed"] == n and res["max_ms"] < 1e3 / 30.0
+    out["paper_scene_1.1MP_16spp_30fps"] = res
+    scenes = S.serving_scenes(8, 1000, 250000, seed=0)
+    be = SV.GpuBackend(local, lam=lam)
+    srv = SV.Server(be, scenes, hbm_budget=int(args.hbm_gb * (1 << 30)))
+    trace = S.poisson_trace(int(round(rate * trace_s)), rate, len(scenes), seed=0)
+    res = replay(srv, SV, trace, scenes, S.PRECISION_FP32)
+    srv.close()
+    be.close()
+    res["rate_req_s"] = rate
+    res["arrivals_s"] = trace_s
+    out["poisson_trace_segment"] = res
+    return out
 
 
 def run_serve(args):
@@ -668,7 +706,7 @@ def main():
         shadowed.params.shadows = True
         pin_aa = S.Workload("paper_26318obj_965x1137_pinhole_aa2x2_spp16", w.scene, W, H, S.Params(ao_samples=16),
                             w.lights, S.pinhole_camera(w.scene, W, H, fov_deg=30.0, aa=2))
-        side = (("fp64_path_1.1MP", S.paper_1mp(precision=other, scene=w.scene), 3),
+        side = (("fp64_path_1.1MP", S.paper_1mp(precision=other, scene=w.scene), 20),
                 ("fp32_path_1.1MP_direct_light_shadows", shadowed, 5),
                 ("fp32_path_1.1MP_pinhole_2x2_supersampled", pin_aa, 3),
                 ("fp32_path_4.4MP", mid, 3),
@@ -687,13 +725,19 @@ def main():
             # rays counted: primary + AO samples of hit pixels (shadow rays, at most one per
             # light per hit, are not counted: Mrays/s of the shadow run is a lower bound)
             rays2 = aa2 * aa2 * wk.width * wk.height + 16 * h2
-            ms2, _ = time_steps(torch, stream, flush,
-                                lambda: G.gbrt_render(r.ctx, scene, grid, c2, wk.width, wk.height, 16, l2, p2, o2),
-                                nsteps, 2)
+            profile = name == "fp64_path_1.1MP"
+            G.gbrt_set_profiling(r.ctx, profile)
+            ms2, ph2 = time_steps(torch, stream, flush,
+                                  lambda: G.gbrt_render(r.ctx, scene, grid, c2, wk.width, wk.height, 16, l2, p2, o2),
+                                  nsteps, 2, after=(lambda: G.gbrt_phase_times(r.ctx)) if profile else None)
+            G.gbrt_set_profiling(r.ctx, False)
             m2 = sum(ms2) / len(ms2)
             extras[name] = {"Mrays_s": round(rays2 / m2 / 1e3, 2), "ms_per_frame": round(m2, 4),
-                            "fps": round(1e3 / m2, 2), "rays_per_frame": rays2,
+                            "fps": round(1e3 / m2, 2), "rays_per_frame": rays2, "steps": nsteps,
                             "dtype": "f64" if wk.params.precision == S.PRECISION_FP64 else "f32"}
+            if profile:
+                extras[name]["phases_ms"] = {k: round(sum(ph[k] for ph in ph2) / len(ph2), 4) for k in G.PHASES}
+                extras[name]["ao_rays_per_frame"] = 16 * h2
         # animated scene: per frame, new geometry from page-locked host memory,
         # a device-side grid rebuild and the render, with no host round trip
         extras["fp32_path_1.1MP_md_animation"] = animation_extra(G, torch, r, w, lam, stream, flush, dev)
@@ -701,11 +745,14 @@ def main():
         extras["resolution_sweep_Mrays_s"] = {"1.1MP": round(value, 1),
                                               "4.4MP": extras["fp32_path_4.4MP"]["Mrays_s"],
                                               "17.6MP": extras["fp32_path_17.6MP"]["Mrays_s"]}
+        # serving: the paper scene streamed at 30 frames/s, and a segment of
+        # the Poisson serving trace (8 resident scenes, 1k-250k objects)
+        extras["serving"] = serving_extra(args, local, w.scene)
 
     cpu = None
     roof = None
     if not args.no_cpu_baseline:
-        s = oracle_sample(w, lam, budget_s=15.0)
+        s = oracle_sample(w, lam, budget_s=10.0)
         cpu = {"value": round(s["rays"] / s["seconds"] / 1e6, 4), "unit": "Mrays/s", "cores": s["cores"],
                "kind": "oracle", "sample": f"{s['rows']} evenly spaced rows ({s['pixels']} px, {s['rays']} rays) "
                                            f"of the 965x1137 frame, FP64 grid walk, lambda {lam}"}
@@ -714,7 +761,7 @@ def main():
                               "sample": f"{s1['rows']} evenly spaced rows ({s1['rays']} rays)"}
         if not args.no_extras and args.workload == "paper_1mp":
             w17 = S.paper_17mp(precision=p.precision, scene=w.scene)
-            s17 = oracle_sample(w17, lam, budget_s=20.0)
+            s17 = oracle_sample(w17, lam, budget_s=10.0)
             cpu["17.6MP"] = {"value": round(s17["rays"] / s17["seconds"] / 1e6, 4), "cores": s17["cores"],
                              "seconds": round(s17["seconds"], 2),
                              "sample": f"{s17['rows']} evenly spaced rows of 4548 ({s17['rays']} rays)"}
@@ -722,21 +769,45 @@ def main():
             # dominant kernel: the AO walk; its algorithmic work per launch is the
             # AO rays of one frame x the oracle's AO flops per ray (same grid lambda)
             fpr, bpr = per_ray_work(s["counters"], "ao")
+            fpr_dev, _ = per_ray_work(s["counters"], "ao", device_formulas=True)
             ao_rays = rays_per_step - W * H
             ao_s = sum(ph["ao_walk"] for ph in phases) / len(phases) / 1e3
             achieved = fpr * ao_rays / ao_s / 1e12
+            l2_gbs = bpr * ao_rays / ao_s / 1e9
             prof = committed_profile(args.workload, args.precision)
             roof = {"bound": "alu", "kernel": "k_ao_walk", "achieved": round(achieved, 3),
                     "peak": round(fp32_peak, 2), "unit": "TFLOP/s", "frac": round(achieved / fp32_peak, 4),
                     "traffic": committed_traffic(args.workload, args.precision),
                     "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 flop x "
                                    f"{sm_max:.0f} MHz ({peak_src} max clock)",
+                    "flops_per_ray": round(fpr, 1),
+                    "flops_convention": f"per AO ray: oracle cells x {FLOPS_CELL} + sphere tests x {FLOPS_SPHERE} "
+                                        f"+ cylinder tests x {FLOPS_CYLINDER} (same lambda)",
+                    "flops_per_ray_device_formulas": round(fpr_dev, 1),
+                    "frac_device_formulas": round(fpr_dev * ao_rays / ao_s / 1e12 / fp32_peak, 4),
                     "issue_slots_busy_ncu": (round(prof["issue_active_pct"] / 100.0, 3)
                                              if "issue_active_pct" in prof else None),
                     "fma_measured_tflops": calib["fp32_fma_tflops"],
                     "frac_of_measured_fma": round(achieved / calib["fp32_fma_tflops"], 4),
-                    "kernel_ms": round(ao_s * 1e3, 4), "flops_per_ray": round(fpr, 1),
-                    "walk_bytes_per_ray": round(bpr, 1), "walk_GBps": round(bpr * ao_rays / ao_s / 1e9, 1)}
+                    "kernel_ms": round(ao_s * 1e3, 4),
+                    "l2": {"bound": "l2", "achieved": round(l2_gbs, 1), "peak": calib["l2_read_gbs"],
+                           "unit": "GB/s", "frac": round(l2_gbs / calib["l2_read_gbs"], 4),
+                           "bytes_per_ray": round(bpr, 1),
+                           "peak_source": "16-byte reads of a buffer of half the L2 (gbrt_microbench, this GPU)"}}
+            fp64 = extras.get("fp64_path_1.1MP")
+            if fp64 and "phases_ms" in fp64:
+                # the plain FP64 path's AO walk against the FP64 FMA rate measured
+                # on this GPU (same algorithmic work per AO ray, its own AO rays)
+                ao64_s = fp64["phases_ms"]["ao_walk"] / 1e3
+                ach64 = fpr * fp64["ao_rays_per_frame"] / ao64_s / 1e12
+                fp64["roofline"] = {"bound": "alu_fp64", "kernel": "k_ao_walk<double>", "achieved": round(ach64, 4),
+                                    "peak": calib["fp64_fma_tflops"], "unit": "TFLOP/s",
+                                    "frac": round(ach64 / calib["fp64_fma_tflops"], 4),
+                                    "peak_source": "FP64 FMA rate measured by gbrt_microbench on this GPU",
+                                    "kernel_ms": round(ao64_s * 1e3, 4), "flops_per_ray": round(fpr, 1),
+                                    "nominal_fp64_tflops": 1.25,
+                                    "frac_of_nominal": round(ach64 / 1.25, 4)}
+                fp64["fp32_path_speedup"] = round(fp64["ms_per_frame"] / ms_step, 2)
 
     config = {"workload": ("orbit64_" if orbit else "") + w.name, "precision": args.precision,
               "grid_lambda": lam, "tuning": G.gbrt_get_tuning(r.ctx), "tuned_by": tuned,

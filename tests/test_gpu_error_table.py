@@ -1,0 +1,119 @@
+"""Error against the FP64 oracle, per workload and precision.
+
+One row per (workload, precision): the small globule at 256x256 (8 spp), the
+paper-sized scene at 965x1137 (16 spp, every pixel), the 256x256 centre crop
+of its 3860x4548 frame, one orbit frame of each orbit size (512x512,
+965x1137, 1920x1080, 8-32 spp), and the smallest and largest scenes of the
+serving set (1k and 250k objects). Each row meets the parity rule; the table
+(non-grazing id mismatches, grazing pixels, fraction of pixels beyond 1/255,
+mean and largest absolute error, AO counts equal) is printed, and written as
+JSON where GBRT_ERROR_TABLE names a file.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_0801_1500_gb300 import scenes as S
+from gpu_common import assert_parity, compare
+
+pytestmark = pytest.mark.gpu
+
+ROWS = []
+
+
+@pytest.fixture(scope="module")
+def G():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0801_1500_gb300 import gbrt
+    return gbrt
+
+
+@pytest.fixture(scope="module")
+def R(G):
+    r = G.Renderer(0)
+    yield r
+    r.close()
+    path = os.environ.get("GBRT_ERROR_TABLE")
+    if path and ROWS:
+        with open(path, "w") as f:
+            json.dump(ROWS, f, indent=1)
+
+
+@pytest.fixture(scope="module")
+def paper():
+    return S.paper_scene(0)
+
+
+@pytest.fixture(scope="module")
+def serving():
+    return S.serving_scenes(8, 1000, 250000, seed=0)
+
+
+def measure(G, R, oracle, name, sc, cam, W, H, p, lam=8.0, pixels=None, oracle_mode="grid"):
+    scene, grid = R.upload(sc, lam=lam)
+    rgb, ids, vis = R.render(scene, grid, cam, W, H, S.default_lights(), p, ids=True, vis=True)
+    G.gbrt_sync(R.ctx)
+    R.free(scene, grid)
+    rgb = rgb.cpu().numpy().reshape(-1, 3).astype(np.float64)
+    ids = ids.cpu().numpy().view(np.uint32).ravel()
+    vis = vis.cpu().numpy().view(np.uint32).ravel()
+    ref = oracle.render(sc, cam, W, H, S.default_lights(), p, pixels=pixels, mode=oracle_mode, lam=2.0)
+    st = compare(rgb, ids, vis, ref, pixels=pixels)
+    row = dict(workload=name, precision="fp64" if p.precision == S.PRECISION_FP64 else "fp32",
+               frame=f"{W}x{H}", spp=p.ao_samples, objects=sc.n_objects, pixels=st["n"],
+               id_mismatch_non_grazing=st["id_mismatch"], grazing=st["grazing"], graze_bad=st["graze_bad"],
+               frac_beyond_1_255=st["frac_bad"], mae=st["mae"], max_err=st["max_err"], ao_counts_equal=st["vis_eq"])
+    ROWS.append(row)
+    print(json.dumps(row))
+    assert_parity(st, name)
+    return st
+
+
+PRECS = [S.PRECISION_FP32, S.PRECISION_FP64]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_small_globule(G, R, oracle, prec):
+    w = S.small_fp64()
+    p = S.Params(ao_samples=8, seed=0, precision=prec)
+    measure(G, R, oracle, "small 2,000+1,900 objects", w.scene, w.camera, w.width, w.height, p, lam=2.0,
+            oracle_mode="brute")
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_paper_scene_1mp(G, R, oracle, paper, prec):
+    p = S.Params(ao_samples=16, seed=0, precision=prec)
+    measure(G, R, oracle, "paper-sized 26,318 objects", paper, S.ortho_camera(paper, 965, 1137), 965, 1137, p)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_paper_scene_17mp_crop(G, R, oracle, paper, prec):
+    W, H = 3860, 4548
+    j0, i0 = H // 2 - 128, W // 2 - 128
+    jj, ii = np.meshgrid(np.arange(j0, j0 + 256), np.arange(i0, i0 + 256), indexing="ij")
+    p = S.Params(ao_samples=16, seed=0, precision=prec)
+    measure(G, R, oracle, "paper-sized, 17.6 MP frame, 256x256 centre crop", paper, S.ortho_camera(paper, W, H),
+            W, H, p, pixels=(jj * W + ii).ravel())
+
+
+@pytest.mark.parametrize("size", [(512, 512), (965, 1137), (1920, 1080)])
+def test_orbit_frames(G, R, oracle, paper, size):
+    frames = [f for f in S.orbit_frames(paper, 64) if (f["width"], f["height"]) == size]
+    f = frames[0]
+    p = S.Params(ao_samples=f["spp"], seed=f["seed"], frame=f["frame"])
+    measure(G, R, oracle, f"orbit frame {f['frame']}", paper, f["camera"], f["width"], f["height"], p)
+
+
+@pytest.mark.parametrize("which", [0, 7])
+@pytest.mark.parametrize("prec", PRECS)
+def test_serving_scenes(G, R, oracle, serving, which, prec):
+    sc = serving[which]
+    W, H = 965, 1137
+    p = S.Params(ao_samples=16, seed=3, precision=prec)
+    pix = np.random.default_rng(which).choice(W * H, 20000, replace=False)
+    measure(G, R, oracle, f"serving scene {which} ({sc.n_objects} objects), 20,000 sampled pixels", sc,
+            S.ortho_camera(sc, W, H, angle_deg=30.0), W, H, p, pixels=pix)
