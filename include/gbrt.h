@@ -393,8 +393,9 @@ GBRT_API int gbrt_get_tuning(const gbrt_ctx* ctx, gbrt_tuning* tuning);
 GBRT_API int gbrt_set_profiling(gbrt_ctx* ctx, int on);
 
 /* Device time in ms of the last timed render's kernels: [0] primary walk and
- * refinement, [1] AO plan, [2] AO shadow-ray walk, [3] shading. Waits for
- * that render. GBRT_EINVAL if no render was timed. */
+ * refinement (its last CTA also lays out the AO pass), [1] 0 (the AO plan has
+ * no kernel of its own), [2] AO shadow-ray walk, [3] shading. Waits for that
+ * render. GBRT_EINVAL if no render was timed. */
 GBRT_API int gbrt_phase_times(gbrt_ctx* ctx, float ms[4]);
 
 /* Micro-benchmarks of the GPU the context runs on (not part of the paper's

@@ -4,8 +4,9 @@
 //   k_primary  persistent; each warp pulls a 32-pixel tile of some frame from
 //              an atomic queue, walks the primary rays (nearest hit), refines
 //              the winner in its object's frame and appends the hit (AO
-//              origin, normal) to its frame's hit list;
-//   k_ao_plan  prefix sums of hits and AO rays per frame;
+//              origin, normal) to its frame's hit list; the last CTA to
+//              finish lays out the AO pass (prefix sums of hits and AO rays
+//              per frame);
 //   k_ao_walk  persistent; each lane holds one AO (or direct-light shadow)
 //              ray; a warp refills its idle lanes together from its ray pool
 //              once fewer than `refill` lanes still hold a ray, walks all of
@@ -18,6 +19,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <functional>
 #include <type_traits>
 #include <vector>
 
@@ -27,6 +29,13 @@
 namespace gbrt {
 
 constexpr unsigned FULL = 0xffffffffu;
+
+// A kernel launched as a programmatic dependent of the previous one in its
+// stream (launch_dependent) starts while that kernel drains; it waits here,
+// before reading anything the previous kernel wrote, until the previous grid
+// has finished and its writes are visible. Without that launch attribute the
+// wait returns at once.
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 // Largest f with off[f] <= x (off nondecreasing, x < off[n]).
 template <class T>
@@ -193,6 +202,25 @@ __device__ __forceinline__ double ao_maxdist<double>(const FrameDev& f) { return
 
 // ---------------------------------------------------------------- primary pass
 
+// Prefix sums of hits and AO rays per frame; resets the AO and shading queues.
+// Run by one thread of the primary pass's last CTA once every CTA's hits are
+// counted (the counts are read through L2: other CTAs added them atomically).
+__device__ __forceinline__ void ao_plan(const BatchDev& b) {
+    unsigned long long jobs = 0, hits = 0;
+    b.job_off[0] = 0;
+    b.hit_off[0] = 0;
+    for (int f = 0; f < b.nframes; ++f) {
+        unsigned long long h = __ldcg(b.hit_count + f);
+        hits += h;
+        jobs += h * (unsigned long long)b.frames[f].jobs_per_hit;
+        b.hit_off[f + 1] = hits;
+        b.job_off[f + 1] = jobs;
+    }
+    b.queue[1] = 0;
+    b.queue[2] = 0;
+}
+
+
 template <int MODE>
 __global__ void __launch_bounds__(256) k_primary(const __grid_constant__ BatchDev b) {
     typedef typename std::conditional<MODE == GBRT_FP32, float, double>::type R;
@@ -284,23 +312,19 @@ __global__ void __launch_bounds__(256) k_primary(const __grid_constant__ BatchDe
         }
     }
     if (overflow) atomicOr(b.err, ERR_DDA_STEPS);
-}
-
-// Prefix sums of hits and AO rays per frame; resets the AO and shading queues.
-__global__ void k_ao_plan(const __grid_constant__ BatchDev b) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    unsigned long long jobs = 0, hits = 0;
-    b.job_off[0] = 0;
-    b.hit_off[0] = 0;
-    for (int f = 0; f < b.nframes; ++f) {
-        unsigned long long h = b.hit_count[f];
-        hits += h;
-        jobs += h * (unsigned long long)b.frames[f].jobs_per_hit;
-        b.hit_off[f + 1] = hits;
-        b.job_off[f + 1] = jobs;
+    // the last CTA to finish lays out the AO pass (queue[3] counts finished
+    // CTAs; it starts at zero with the batch's counters)
+    __shared__ bool last_cta;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last_cta = atomicAdd(b.queue + 3, 1ull) == (unsigned long long)gridDim.x - 1ull;
     }
-    b.queue[1] = 0;
-    b.queue[2] = 0;
+    __syncthreads();
+    if (last_cta && threadIdx.x == 0) {
+        __threadfence();
+        ao_plan(b);
+    }
 }
 
 // ---------------------------------------------------------------- AO pass
@@ -504,6 +528,7 @@ template <class R, bool UNI>
 __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDev b) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     AoWarp<R, UNI>& S = reinterpret_cast<AoWarp<R, UNI>*>(smem_raw)[threadIdx.x >> 5];
+    grid_dependency_wait();
     ObjPtr<R> uobj = nullptr;
     const uint32_t* uitems = nullptr;
     const uint2* ucells = nullptr;
@@ -730,6 +755,7 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
 
 template <class R>
 __global__ void __launch_bounds__(256) k_shade(const __grid_constant__ BatchDev b) {
+    grid_dependency_wait();
     const unsigned long long total = b.hit_off[b.nframes];
     for (unsigned long long g = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; g < total;
          g += (unsigned long long)gridDim.x * blockDim.x) {
@@ -779,6 +805,7 @@ __global__ void k_patch_grids(const __grid_constant__ BatchDev b) {
 // Frames are strided over blockIdx.y; frames without supersampling are skipped.
 template <class R>
 __global__ void __launch_bounds__(256) k_resolve(const __grid_constant__ BatchDev b) {
+    grid_dependency_wait();
     for (int f = blockIdx.y; f < b.nframes; f += gridDim.y) {
         const FrameDev& F = b.frames[f];
         const int m = F.aa;
@@ -873,6 +900,24 @@ struct Grids {
     int primary, ao, shade, resolve;
 };
 
+// Launch `kernel` as a programmatic dependent of the kernel before it in
+// `stream`: its CTAs may be scheduled while that kernel drains, and they wait
+// (grid_dependency_wait) for its results before reading them.
+static cudaError_t launch_dependent(void (*kernel)(BatchDev), dim3 grid, dim3 block, size_t smem,
+                                    cudaStream_t stream, const BatchDev& bd) {
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, bd);
+}
+
 // The AO walk of one precision and scene layout (UNI: one scene and grid for
 // the whole batch) with its dynamic shared memory; launched with an explicit
 // grid, or with one sized for the current device (grid <= 0).
@@ -881,7 +926,28 @@ static size_t ao_smem(int block) {
     return (size_t)(block / 32) * sizeof(AoWarp<R, UNI>);
 }
 
+// Shared-memory share of the SM asked for the FP32 walk: just enough for four
+// resident CTAs of 256 threads (and the driver's per-CTA reservation), so the
+// rest of the SM's 256 KB serves as L1 for the walk's cell, item and object
+// loads (the 100 KB configuration instead of the 132 KB one the driver picks
+// by default: AO walk 1.185 -> 1.176 ms on the paper frame).
+template <bool UNI>
+static cudaError_t prefer_small_carveout() {
+    int dev = 0, per_sm = 0, reserved = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    if (e != cudaSuccess || per_sm <= 0) return e;
+    const long long need = 4ll * ((long long)ao_smem<float, UNI>(256) + reserved);
+    const int pct = (int)std::min<long long>(100, (need * 100 + per_sm - 1) / per_sm);
+    return cudaFuncSetAttribute(k_ao_walk<float, UNI>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+}
+
 static cudaError_t set_ao_smem_limits() {
+    // a refused preference leaves the driver's choice (and its error is
+    // cleared here, so it is not taken for a later launch's)
+    if (prefer_small_carveout<true>() != cudaSuccess || prefer_small_carveout<false>() != cudaSuccess)
+        (void)cudaGetLastError();
     // the AO kernels' per-warp staging can exceed the 48 KB default
     cudaError_t e = cudaFuncSetAttribute(k_ao_walk<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)ao_smem<float, false>(256));
@@ -904,8 +970,20 @@ static int ao_grid(Ctx* ctx, int block) {
 
 template <class R>
 static void launch_ao(const BatchDev& bd, bool uni, int grid, int block, cudaStream_t stream) {
-    if (uni) k_ao_walk<R, true><<<grid, block, ao_smem<R, true>(block), stream>>>(bd);
-    else k_ao_walk<R, false><<<grid, block, ao_smem<R, false>(block), stream>>>(bd);
+    if (uni) launch_dependent(k_ao_walk<R, true>, grid, block, ao_smem<R, true>(block), stream, bd);
+    else launch_dependent(k_ao_walk<R, false>, grid, block, ao_smem<R, false>(block), stream, bd);
+}
+
+// The passes after the primary one: AO walk, shading, and the box filter of
+// supersampled frames (the AO plan runs in the primary kernel's last CTA).
+template <class R>
+static void launch_after_primary(const BatchDev& bd, bool uni, int ao_grid, int block, int shade_grid,
+                                 int resolve_grid, bool resolve, cudaStream_t stream,
+                                 const std::function<void(int)>& mark) {
+    launch_ao<R>(bd, uni, ao_grid, block, stream);
+    mark(3);
+    launch_dependent(k_shade<R>, shade_grid, 256, 0, stream, bd);
+    if (resolve) launch_dependent(k_resolve<R>, dim3(resolve_grid, std::min(bd.nframes, 65535)), 256, 0, stream, bd);
 }
 
 static Grids grids_for(Ctx* ctx, int precision, bool uni) {
@@ -960,28 +1038,21 @@ static int enqueue_batch(Ctx* ctx, cudaStream_t stream, int precision, const Bat
         if (tm) cudaEventRecord(ctx->ev[k], stream);
     };
     mark(0);
+    const bool uni = (extra & EXTRA_UNI) != 0;
     if (precision == GBRT_FP32) {
         k_primary<GBRT_FP32><<<gr.primary, block, 0, stream>>>(bd);
         mark(1);
-        k_ao_plan<<<1, 32, 0, stream>>>(bd);
         mark(2);
-        launch_ao<float>(bd, (extra & EXTRA_UNI) != 0, gr.ao, block, stream);
-        mark(3);
-        k_shade<float><<<gr.shade, 256, 0, stream>>>(bd);
-        if (resolve) k_resolve<float><<<dim3(gr.resolve, std::min(bd.nframes, 65535)), 256, 0, stream>>>(bd);
+        launch_after_primary<float>(bd, uni, gr.ao, block, gr.shade, gr.resolve, resolve, stream, mark);
     } else {
         k_primary<GBRT_FP64><<<gr.primary, block, 0, stream>>>(bd);
         mark(1);
-        k_ao_plan<<<1, 32, 0, stream>>>(bd);
         mark(2);
-        launch_ao<double>(bd, (extra & EXTRA_UNI) != 0, gr.ao, block, stream);
-        mark(3);
-        k_shade<double><<<gr.shade, 256, 0, stream>>>(bd);
-        if (resolve) k_resolve<double><<<dim3(gr.resolve, std::min(bd.nframes, 65535)), 256, 0, stream>>>(bd);
+        launch_after_primary<double>(bd, uni, gr.ao, block, gr.shade, gr.resolve, resolve, stream, mark);
     }
     mark(4);
     if (tm) ctx->timed = true;
-    ctx->launches += resolve ? 5 : 4;
+    ctx->launches += resolve ? 4 : 3;
     return err_of(cudaGetLastError());
 }
 
@@ -1103,7 +1174,7 @@ int render_frames(Ctx* ctx, FrameDev* frames, int n, bool use_graph) {
             ctx->graph_bd = bd;
         }
         rc = err_of(cudaGraphLaunch(ctx->graph_exec, ctx->stream));
-        ctx->launches += 4 + (resolve ? 1 : 0) + ((extra & EXTRA_PATCH) ? 1 : 0);
+        ctx->launches += 3 + (resolve ? 1 : 0) + ((extra & EXTRA_PATCH) ? 1 : 0);
     }
     if (rc != GBRT_OK) return rc;
     cudaEventRecord(ctx->staging_done, ctx->stream);
@@ -1122,16 +1193,15 @@ int enqueue_prepared(const BatchDev& bd, int precision, cudaStream_t stream, int
     };
     // one frame: one scene and grid
     if (patch) k_patch_grids<<<1, 128, 0, stream>>>(bd);
+    const auto none = [](int) {};
     if (precision == GBRT_FP32) {
         k_primary<GBRT_FP32><<<grid_of(k_primary<GBRT_FP32>, 0), block, 0, stream>>>(bd);
-        k_ao_plan<<<1, 32, 0, stream>>>(bd);
-        launch_ao<float>(bd, true, grid_of(k_ao_walk<float, true>, ao_smem<float, true>(block)), block, stream);
-        k_shade<float><<<num_sms * 8, 256, 0, stream>>>(bd);
+        launch_after_primary<float>(bd, true, grid_of(k_ao_walk<float, true>, ao_smem<float, true>(block)), block,
+                                    num_sms * 8, 0, false, stream, none);
     } else {
         k_primary<GBRT_FP64><<<grid_of(k_primary<GBRT_FP64>, 0), block, 0, stream>>>(bd);
-        k_ao_plan<<<1, 32, 0, stream>>>(bd);
-        launch_ao<double>(bd, true, grid_of(k_ao_walk<double, true>, ao_smem<double, true>(block)), block, stream);
-        k_shade<double><<<num_sms * 8, 256, 0, stream>>>(bd);
+        launch_after_primary<double>(bd, true, grid_of(k_ao_walk<double, true>, ao_smem<double, true>(block)), block,
+                                     num_sms * 8, 0, false, stream, none);
     }
     return err_of(cudaGetLastError());
 }
