@@ -224,7 +224,8 @@ __device__ __forceinline__ bool clip_grid(const GridDev& g, V3<R> o, V3<R> d, R 
 // Amanatides & Woo (1987) traversal state: the current cell's index, per
 // axis the index change of one step, the t of the next boundary crossing and
 // the t between crossings; the end of the clipped interval and the number of
-// cells (the walk's bounds).
+// cells (the walk's bounds); `left` counts down the steps (or, in the AO walk,
+// the lockstep iterations) a walk may take: nx + ny + nz + 3.
 template <class R>
 struct Walk {
     int stx, sty, stz;
@@ -283,9 +284,8 @@ __device__ __forceinline__ R walk_cell_exit(const Walk<R>& w) {
 }
 
 // Step to the next cell (ties: x, then y, then z). False when the walk leaves
-// the clipped interval or the grid's index range; sets *overflow past the step
-// bound. Written with selects rather than a branch per axis: the lanes of a
-// warp step along different axes.
+// the clipped interval or the grid's index range. Written with selects rather
+// than a branch per axis: the lanes of a warp step along different axes.
 //
 // The clipped interval ends inside the grid, so in exact arithmetic no step
 // leaves it. Rounding in the accumulated crossings can carry the last one or
@@ -295,11 +295,7 @@ __device__ __forceinline__ R walk_cell_exit(const Walk<R>& w) {
 // point inside the grid, in a cell the walk visits before, and a test of any
 // other object finds only true intersections.
 template <class R>
-__device__ __forceinline__ bool walk_next(Walk<R>& w, bool& overflow) {
-    if (--w.left <= 0) {
-        overflow = true;
-        return false;
-    }
+__device__ __forceinline__ bool walk_step(Walk<R>& w) {
     const bool bx = w.tnx <= w.tny && w.tnx <= w.tnz;
     const bool by = !bx && w.tny <= w.tnz;
     const bool bz = !bx && !by;
@@ -310,6 +306,17 @@ __device__ __forceinline__ bool walk_next(Walk<R>& w, bool& overflow) {
     w.tnz = bz ? w.tnz + w.tdz : w.tnz;
     w.cell += bx ? w.stx : (by ? w.sty : w.stz);
     return (unsigned)w.cell < w.ncells;
+}
+
+// walk_step within the walk's step bound: past it (only a walk whose crossing
+// times are not numbers can get there) the walk ends and *overflow is set.
+template <class R>
+__device__ __forceinline__ bool walk_next(Walk<R>& w, bool& overflow) {
+    if (--w.left <= 0) {
+        overflow = true;
+        return false;
+    }
+    return walk_step(w);
 }
 
 // ---------------------------------------------------------------- traversal

@@ -421,7 +421,7 @@ struct __align__(16) AoRay {
 // cells each active ray takes per lockstep iteration: further cells while it
 // holds fewer than AO_MIN_PAIRS candidates, at most AO_CELLS
 constexpr int AO_CELLS = 4;
-constexpr unsigned AO_MIN_PAIRS = 6;
+constexpr unsigned AO_MIN_PAIRS = 8;
 // AO rays a warp claims from the global queue at once (its local pool)
 constexpr unsigned AO_CLAIM = 64;
 
@@ -620,6 +620,15 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
         //    once is exact). The ray's fifo is first topped up to AO_CELLS
         //    loaded cells -- the new cells' loads are independent and overlap
         //    -- and the cells it does not take wait there for the next iteration
+        // the walk's bound, counted per iteration rather than per step (every
+        // iteration takes at least one cell or ends the ray, so a walk of the
+        // grid's nx + ny + nz + 1 cells never reaches it; one whose crossing
+        // times are not numbers ends here)
+        if (has && --w.left <= 0) {
+            overflow = true;
+            wend = true;
+            nf = 0;
+        }
         bool ending = false;
         unsigned kg[AO_CELLS], ng[AO_CELLS];
         unsigned avail = 0u;
@@ -633,7 +642,7 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
                 } else if (!wend) {
                     bool next = fresh;
                     fresh = false;
-                    if (!next) next = walk_next(w, overflow);
+                    if (!next) next = walk_step(w);
                     if (next) {
                         cr = __ldg(cells + w.cell);
                         ++avail;
