@@ -541,7 +541,7 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
     const unsigned lt = (1u << lane) - 1u;
     const unsigned long long total = b.job_off[b.nframes];
     const int refill = b.refill;
-    bool has = false, fresh = false, exhausted = false, overflow = false;
+    bool has = false, exhausted = false, overflow = false;
     Walk<R> w;
     unsigned nf = 0;      // cells waiting in this lane's fifo
     bool wend = false;    // the walk has no further cells
@@ -597,10 +597,12 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
                             // behind a convex outer side the ray cannot meet it again)
                             if (J.self != GBRT_MISS) S.mbox[lane][J.self & (AoCfg<R>::mbox - 1)] = J.self;
                         }
-                        nf = 0;
+                        // the walk stands on its first cell: its record waits in
+                        // the fifo, so every later cell comes from a step
+                        S.fifo[lane][0] = __ldg(cells + w.cell);
+                        nf = 1;
                         wend = false;
                         has = true;
-                        fresh = true;  // the walk stands on its first cell, not yet loaded
                     } else {
                         ao_escape(b, vslot, lbit);  // misses the objects' bounds: escapes
                     }
@@ -640,10 +642,7 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
                     cr = S.fifo[lane][g];
                     ++avail;
                 } else if (!wend) {
-                    bool next = fresh;
-                    fresh = false;
-                    if (!next) next = walk_step(w);
-                    if (next) {
+                    if (walk_step(w)) {
                         cr = __ldg(cells + w.cell);
                         ++avail;
                     } else {
@@ -654,28 +653,18 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
             kg[g] = cr.x;
             ng[g] = cr.y;
         }
-        if (has && avail == 0u) {
-            // walked out: escapes
-            if (lbit) atomicOr(b.lmask + vslot, lbit);
-            else atomicAdd(b.vis + vslot, 1u);
-            has = false;
-        }
         if (has) {
             // take cells 0..m-1; the rest go back to the fifo
-            unsigned m = 1u, sofar = ng[0];
+            // m = 1 + the number of prefixes (cells 0..g-1, g < avail) still
+            // below AO_MIN_PAIRS candidates: both conditions only turn false
+            // (m = 0 when the walk has no cell left: the ray escapes below)
+            const unsigned c1 = ng[0], c2 = c1 + ng[1], c3 = c2 + ng[2];
+            const unsigned m = (avail > 0u) + (avail > 1u && c1 < AO_MIN_PAIRS) + (avail > 2u && c2 < AO_MIN_PAIRS) +
+                               (avail > 3u && c3 < AO_MIN_PAIRS);
 #pragma unroll
             for (int g = 1; g < AO_CELLS; ++g) {
-                if ((unsigned)g < avail && sofar < AO_MIN_PAIRS && m == (unsigned)g) {
-                    sofar += ng[g];
-                    m = (unsigned)g + 1u;
-                }
-            }
-#pragma unroll
-            for (int g = 1; g < AO_CELLS; ++g) {
-                if ((unsigned)g >= m) {
-                    if ((unsigned)g < avail) S.fifo[lane][g - m] = make_uint2(kg[g], ng[g]);
-                    ng[g] = 0u;
-                }
+                if ((unsigned)g >= m && (unsigned)g < avail) S.fifo[lane][g - m] = make_uint2(kg[g], ng[g]);
+                ng[g] = (unsigned)g >= m ? 0u : ng[g];
             }
             nf = avail - m;
             ending = wend && nf == 0u;  // escapes unless this iteration's tests hit
