@@ -347,7 +347,7 @@ struct AoJob {
 // stays clear).
 template <class R>
 __device__ __forceinline__ bool ao_job(const BatchDev& b, unsigned long long jj, AoJob<R>& J) {
-    const int f = find_frame(b.job_off, b.nframes, jj);
+    const int f = b.nframes == 1 ? 0 : find_frame(b.job_off, b.nframes, jj);
     const FrameDev& F = b.frames[f];
     J.F = &F;
     const unsigned long long jl = jj - b.job_off[f];
@@ -637,19 +637,13 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
 #pragma unroll
         for (int g = 0; g < AO_CELLS; ++g) {
             uint2 cr = make_uint2(0u, 0u);
-            if (has) {
-                if (g < AO_CELLS - 1 && (unsigned)g < nf) {
-                    cr = S.fifo[lane][g];
-                    ++avail;
-                } else if (!wend) {
-                    if (walk_step(w)) {
-                        cr = __ldg(cells + w.cell);
-                        ++avail;
-                    } else {
-                        wend = true;
-                    }
-                }
+            const bool queued = has && g < AO_CELLS - 1 && (unsigned)g < nf;
+            if (queued) cr = S.fifo[lane][g];
+            if (has && !queued && !wend) {
+                if (walk_step(w)) cr = __ldg(cells + w.cell);
+                else wend = true;
             }
+            if (has && (queued || !wend)) avail = (unsigned)g + 1u;
             kg[g] = cr.x;
             ng[g] = cr.y;
         }
@@ -737,11 +731,9 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
             }
         }
         // 5. any hit occludes the ray; a ray whose walk ended escapes
-        if (has && ((hitbits >> lane) & 1u)) {
-            has = false;
-        } else if (has && ending) {
-            if (lbit) atomicOr(b.lmask + vslot, lbit);
-            else atomicAdd(b.vis + vslot, 1u);
+        const bool occluded = (hitbits >> lane) & 1u;
+        if (has && (occluded || ending)) {
+            if (!occluded) ao_escape(b, vslot, lbit);
             has = false;
         }
         __syncwarp();
