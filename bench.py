@@ -47,6 +47,7 @@ FLOPS_SPHERE_DEVICE, FLOPS_CYLINDER_DEVICE = 24, 58
 # record (16 B) or a cylinder record (32 B)
 BYTES_CELL, BYTES_ITEM, BYTES_SPHERE, BYTES_CYLINDER = 8, 4, 16, 32
 L2_FLUSH_BYTES = 512 << 20   # > 126 MB L2
+PROFILE_EVERY = 10           # timed steps per step with per-kernel events
 
 
 def workload(name, precision):
@@ -279,8 +280,10 @@ def orbit_items(G, torch, dev, scene_h, grid_h, sc, lights, precision, n_frames=
     return frames, items, outs
 
 
-def time_steps(torch, stream, flush, step, steps, warmup, after=None):
-    """Per-step device times (ms): L2 flush outside the events."""
+def time_steps(torch, stream, flush, step, steps, warmup, after=None, before=None, every=1):
+    """Per-step device times (ms): L2 flush outside the events. On every
+    `every`-th step, `before(True)` runs before it and `after()` after it
+    (their results are returned); `before(False)` before the others."""
     for _ in range(warmup):
         flush.zero_()
         step()
@@ -289,11 +292,14 @@ def time_steps(torch, stream, flush, step, steps, warmup, after=None):
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     extra = []
     for k in range(steps):
+        picked = k % every == 0
+        if before is not None:
+            before(picked)
         flush.zero_()
         starts[k].record(stream)
         step()
         ends[k].record(stream)
-        if after is not None:
+        if after is not None and picked:
             extra.append(after())
     torch.cuda.synchronize()
     return [a.elapsed_time(b) for a, b in zip(starts, ends)], extra
@@ -552,7 +558,7 @@ def main():
                                args.steps, args.warmup)
             barrier()
             wall = time.perf_counter() - t0
-        phases = None
+        phases = phases_all = None
     else:
         rgb, ids, _ = r.render(scene, grid, w.camera, W, H, w.lights, p, ids=True)
         G.gbrt_sync(r.ctx)
@@ -562,22 +568,31 @@ def main():
         out = torch.empty((H, W, 3), dtype=torch.float64 if p.precision == S.PRECISION_FP64 else torch.float32,
                           device=dev)
         cam, li, pa = G.make_camera(w.camera), G.make_lights(w.lights), G.make_params(p)
-        G.gbrt_set_profiling(r.ctx, True)
+        # per-kernel CUDA events on every PROFILE_EVERY-th step of the timed
+        # region (the roofline's AO-walk time and the split per kernel): an
+        # event between two kernels costs a few microseconds and the overlap
+        # of the dependent launch, so the other steps run without them
         barrier()
         launches0 = G.gbrt_launch_count(r.ctx)
         with ClockSampler(local) as clk:
             t0 = time.perf_counter()
             ms, phases = time_steps(torch, stream, flush,
                                     lambda: G.gbrt_render(r.ctx, scene, grid, cam, W, H, spp, li, pa, out),
-                                    args.steps, args.warmup, after=lambda: G.gbrt_phase_times(r.ctx))
+                                    args.steps, args.warmup, after=lambda: G.gbrt_phase_times(r.ctx),
+                                    before=lambda on: G.gbrt_set_profiling(r.ctx, on), every=PROFILE_EVERY)
             barrier()
             wall = time.perf_counter() - t0
+        launches1 = G.gbrt_launch_count(r.ctx)
         G.gbrt_set_profiling(r.ctx, False)
+        phases_all = phases
     rc = G.gbrt_sync(r.ctx, check=False)
     if rc != G.OK:
         raise SystemExit(f"render reported {G.strerror(rc)}")
-    # kernels the library launched per timed step (warm-up steps ran in the same window)
-    launches = (G.gbrt_launch_count(r.ctx) - launches0) * args.steps // (args.steps + args.warmup)
+    # kernels the library launched per timed step (warm-up steps ran in the same window;
+    # the separate per-kernel pass after it is not counted)
+    if orbit:
+        launches1 = G.gbrt_launch_count(r.ctx)
+    launches = (launches1 - launches0) * args.steps // (args.steps + args.warmup)
     dev_s = sum(ms) / 1e3
     from paper_0801_1500_gb300 import partition
     t_max = partition.max_over_ranks(dev_s)
@@ -820,8 +835,10 @@ def main():
             "fps": round(frames_per_step * 1e3 / ms_step, 2), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
             "config": config, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-            "phases_ms": ({k: round(sum(ph[k] for ph in phases) / len(phases), 4) for k in G.PHASES}
+            "phases_ms": ({k: round(sum(ph[k] for ph in phases_all) / len(phases_all), 4) for k in G.PHASES}
                           if phases else None),
+            "phases_note": (f"CUDA events between the kernels on every {PROFILE_EVERY}th timed step "
+                            "(the roofline's kernel_ms is their AO-walk mean)") if phases else None,
             "extras": extras or None, "calibration": calib, "wall_s_timed_region": round(wall, 4),
             "clocks": clk.summary()}
     print(json.dumps(line), flush=True)

@@ -387,15 +387,22 @@ GBRT_API int gbrt_render_noalloc(const gbrt_scene* scene, const gbrt_grid* grid,
 GBRT_API int gbrt_set_tuning(gbrt_ctx* ctx, const gbrt_tuning* tuning);
 GBRT_API int gbrt_get_tuning(const gbrt_ctx* ctx, gbrt_tuning* tuning);
 
-/* Per-kernel timing (phase timers): while on, renders record
- * CUDA events between their kernels on the context's stream (renders replayed
- * from a CUDA graph are not timed). */
-GBRT_API int gbrt_set_profiling(gbrt_ctx* ctx, int on);
+/* Per-kernel timing (phase timers). mode 0: off. GBRT_PROFILE_ALL (or any
+ * other non-zero value): renders record CUDA events between all their kernels
+ * on the context's stream. GBRT_PROFILE_AO_WALK: events only just before and
+ * after the AO shadow-ray walk -- each event between two kernels costs a few
+ * microseconds and the overlap of the dependent launch, so this mode times
+ * the dominant kernel with the least disturbance. Renders replayed from a
+ * CUDA graph are not timed. */
+#define GBRT_PROFILE_ALL 1
+#define GBRT_PROFILE_AO_WALK 2
+GBRT_API int gbrt_set_profiling(gbrt_ctx* ctx, int mode);
 
 /* Device time in ms of the last timed render's kernels: [0] primary walk and
  * refinement (its last CTA also lays out the AO pass), [1] 0 (the AO plan has
- * no kernel of its own), [2] AO shadow-ray walk, [3] shading. Waits for that
- * render. GBRT_EINVAL if no render was timed. */
+ * no kernel of its own), [2] AO shadow-ray walk, [3] shading; under
+ * GBRT_PROFILE_AO_WALK only [2] is measured and the others are -1. Waits for
+ * that render. GBRT_EINVAL if no render was timed. */
 GBRT_API int gbrt_phase_times(gbrt_ctx* ctx, float ms[4]);
 
 /* Micro-benchmarks of the GPU the context runs on (not part of the paper's

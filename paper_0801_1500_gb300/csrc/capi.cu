@@ -580,20 +580,25 @@ GBRT_API int gbrt_get_tuning(const gbrt_ctx* ctx, gbrt_tuning* t) {
     return GBRT_OK;
 }
 
-GBRT_API int gbrt_set_profiling(gbrt_ctx* ctx, int on) {
+GBRT_API int gbrt_set_profiling(gbrt_ctx* ctx, int mode) {
     if (!ctx) return GBRT_EINVAL;
     DeviceGuard g(ctx->device);
-    if (on && !ctx->ev[0]) {
+    if (mode && !ctx->ev[0]) {
         for (int k = 0; k < 5; ++k)
             if (cudaEventCreate(&ctx->ev[k]) != cudaSuccess) return GBRT_EDEVICE;
     }
-    ctx->profiling = on != 0;
+    ctx->profiling = mode == 0 ? 0 : (mode == GBRT_PROFILE_AO_WALK ? GBRT_PROFILE_AO_WALK : GBRT_PROFILE_ALL);
     return GBRT_OK;
 }
 
 GBRT_API int gbrt_phase_times(gbrt_ctx* ctx, float ms[4]) {
     if (!ctx || !ms || !ctx->timed) return GBRT_EINVAL;
     DeviceGuard g(ctx->device);
+    if (ctx->timed == GBRT_PROFILE_AO_WALK) {
+        if (cudaEventSynchronize(ctx->ev[3]) != cudaSuccess) return GBRT_EDEVICE;
+        ms[0] = ms[1] = ms[3] = -1.0f;
+        return cudaEventElapsedTime(ms + 2, ctx->ev[2], ctx->ev[3]) == cudaSuccess ? GBRT_OK : GBRT_EDEVICE;
+    }
     if (cudaEventSynchronize(ctx->ev[4]) != cudaSuccess) return GBRT_EDEVICE;
     for (int k = 0; k < 4; ++k)
         if (cudaEventElapsedTime(ms + k, ctx->ev[k], ctx->ev[k + 1]) != cudaSuccess) return GBRT_EDEVICE;

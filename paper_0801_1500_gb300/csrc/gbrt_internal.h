@@ -54,9 +54,10 @@ struct Ctx {
     long long graph_key = 0;
     int graph_extra = 0;  // optional passes in the captured graph (EXTRA_* bits)
     BatchDev graph_bd{};
-    // per-kernel timing
-    bool profiling = false;
-    bool timed = false;
+    // per-kernel timing: 0 off, GBRT_PROFILE_ALL, GBRT_PROFILE_AO_WALK; the
+    // mode the last timed render ran under (0: none timed)
+    int profiling = 0;
+    int timed = 0;
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 

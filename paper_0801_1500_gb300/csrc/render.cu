@@ -1022,10 +1022,12 @@ static int enqueue_batch(Ctx* ctx, cudaStream_t stream, int precision, const Bat
         k_patch_grids<<<1, 128, 0, stream>>>(bd);
         ctx->launches++;
     }
-    // events between the kernels when timing (never inside a graph capture)
-    const bool tm = ctx->profiling && stream == ctx->stream;
+    // events between the kernels when timing (never inside a graph capture);
+    // the AO-walk mode records only events 2 and 3, around the AO walk
+    const int tm = stream == ctx->stream ? ctx->profiling : 0;
     auto mark = [&](int k) {
-        if (tm) cudaEventRecord(ctx->ev[k], stream);
+        if (tm == GBRT_PROFILE_ALL || (tm == GBRT_PROFILE_AO_WALK && (k == 2 || k == 3)))
+            cudaEventRecord(ctx->ev[k], stream);
     };
     mark(0);
     const bool uni = (extra & EXTRA_UNI) != 0;
@@ -1041,7 +1043,7 @@ static int enqueue_batch(Ctx* ctx, cudaStream_t stream, int precision, const Bat
         launch_after_primary<double>(bd, uni, gr.ao, block, gr.shade, gr.resolve, resolve, stream, mark);
     }
     mark(4);
-    if (tm) ctx->timed = true;
+    if (tm) ctx->timed = tm;
     ctx->launches += resolve ? 4 : 3;
     return err_of(cudaGetLastError());
 }

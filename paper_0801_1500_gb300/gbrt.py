@@ -375,8 +375,15 @@ def gbrt_get_tuning(ctx):
     return dict(tile_w=t.tile_w, tile_h=t.tile_h, block=t.block, ctas_per_sm=t.ctas_per_sm, refill=t.refill)
 
 
-def gbrt_set_profiling(ctx, on=True):
-    return _check(lib.gbrt_set_profiling(ctx, 1 if on else 0), "gbrt_set_profiling")
+PROFILE_ALL = 1
+PROFILE_AO_WALK = 2
+
+
+def gbrt_set_profiling(ctx, on=True, ao_walk_only=False):
+    """Per-kernel CUDA events: off, around every kernel, or (ao_walk_only)
+    only around the AO walk."""
+    mode = 0 if not on else (PROFILE_AO_WALK if ao_walk_only else PROFILE_ALL)
+    return _check(lib.gbrt_set_profiling(ctx, mode), "gbrt_set_profiling")
 
 
 PHASES = ("primary", "ao_plan", "ao_walk", "shade")

@@ -42,6 +42,8 @@ def test_version_and_errors(G):
     for code in (G.OK, G.EINVAL, G.ENOMEM, G.EDEVICE, G.ETIMEDOUT, G.ETRAVERSAL):
         assert G.strerror(code) and G.strerror(code) != "unknown error"
     assert G.strerror(-99) == "unknown error"
+    assert G.PROFILE_ALL == int(re.search(r"#define GBRT_PROFILE_ALL (\d+)", text).group(1))
+    assert G.PROFILE_AO_WALK == int(re.search(r"#define GBRT_PROFILE_AO_WALK (\d+)", text).group(1))
 
 
 def test_struct_layout_matches_header(G):

@@ -429,3 +429,38 @@ def test_largest_serving_scene(G, R, oracle, lam):
     assert st["vis_eq"] >= 0.999
     assert 0.3 < (ref["id"] != 0xFFFFFFFF).mean() < 0.95
     R.free(scene, grid)
+
+
+def test_phase_times_in_both_profiling_modes(G, R):
+    # all kernels timed: the primary, AO walk and shading times are positive
+    # and the AO plan (inside the primary kernel) is 0; AO-walk mode: only the
+    # AO walk is timed, close to its time in the full mode
+    import torch
+    sc = S.globule(2000, 1900, 25.0, seed=0)
+    W, H = 256, 256
+    cam = S.ortho_camera(sc, W, H)
+    p = S.Params(ao_samples=8, seed=0)
+    scene, grid = R.upload(sc, lam=8.0)
+    out = torch.empty((H, W, 3), device="cuda")
+    args = (R.ctx, scene, grid, G.make_camera(cam), W, H, 8, G.make_lights(S.default_lights()), G.make_params(p), out)
+    with pytest.raises(G.GbrtError):
+        fresh = G.Renderer(0)
+        try:
+            G.gbrt_phase_times(fresh.ctx)   # nothing timed yet
+        finally:
+            fresh.close()
+    times = {}
+    for mode in ("all", "ao_walk"):
+        G.gbrt_set_profiling(R.ctx, True, ao_walk_only=mode == "ao_walk")
+        runs = []
+        for _ in range(5):
+            G.gbrt_render(*args)
+            runs.append(G.gbrt_phase_times(R.ctx))
+        G.gbrt_set_profiling(R.ctx, False)
+        times[mode] = runs[-1]
+    a, w = times["all"], times["ao_walk"]
+    assert a["primary"] > 0 and a["ao_walk"] > 0 and a["shade"] > 0 and a["ao_plan"] >= 0
+    assert w["primary"] == -1 and w["ao_plan"] == -1 and w["shade"] == -1 and w["ao_walk"] > 0
+    assert 0.5 * a["ao_walk"] < w["ao_walk"] < 2.0 * a["ao_walk"]
+    G.gbrt_sync(R.ctx)
+    R.free(scene, grid)
