@@ -419,9 +419,8 @@ struct __align__(16) AoRay {
 //   q              (FP64 path) surviving (ray, object) pairs waiting for a
 //                  full test batch
 // cells each active ray takes per lockstep iteration: further cells while it
-// holds fewer than AO_MIN_PAIRS candidates, at most AO_CELLS
+// holds fewer than AoCfg<R>::min_pairs candidates, at most AO_CELLS
 constexpr int AO_CELLS = 4;
-constexpr unsigned AO_MIN_PAIRS = 8;
 // AO rays a warp claims from the global queue at once (its local pool)
 constexpr unsigned AO_CLAIM = 64;
 
@@ -439,11 +438,13 @@ template <>
 struct AoCfg<float> {
     static constexpr int mbox = 0;
     static constexpr bool queue = false;
+    static constexpr unsigned min_pairs = 8;  // 6: 0.5% slower, 12: 1.5% slower
 };
 template <>
 struct AoCfg<double> {
     static constexpr int mbox = 8;
     static constexpr bool queue = true;
+    static constexpr unsigned min_pairs = 4;  // 3: 0.4% slower, 6: 2.1%, 8: 5.0%
 };
 
 template <class R, bool Q = AoCfg<R>::queue>
@@ -617,7 +618,7 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
         }
         if (exhausted && __ballot_sync(FULL, has) == 0) break;
         // 2. every active ray takes its next cells: its first, and further ones
-        //    while it holds fewer than AO_MIN_PAIRS candidates (an any-hit
+        //    while it holds fewer than min_pairs candidates (an any-hit
         //    query may test objects past its first hit, so taking several at
         //    once is exact). The ray's fifo is first topped up to AO_CELLS
         //    loaded cells -- the new cells' loads are independent and overlap
@@ -650,11 +651,11 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
         if (has) {
             // take cells 0..m-1; the rest go back to the fifo
             // m = 1 + the number of prefixes (cells 0..g-1, g < avail) still
-            // below AO_MIN_PAIRS candidates: both conditions only turn false
+            // below min_pairs candidates: both conditions only turn false
             // (m = 0 when the walk has no cell left: the ray escapes below)
             const unsigned c1 = ng[0], c2 = c1 + ng[1], c3 = c2 + ng[2];
-            const unsigned m = (avail > 0u) + (avail > 1u && c1 < AO_MIN_PAIRS) + (avail > 2u && c2 < AO_MIN_PAIRS) +
-                               (avail > 3u && c3 < AO_MIN_PAIRS);
+            constexpr unsigned MP = AoCfg<R>::min_pairs;
+            const unsigned m = (avail > 0u) + (avail > 1u && c1 < MP) + (avail > 2u && c2 < MP) + (avail > 3u && c3 < MP);
 #pragma unroll
             for (int g = 1; g < AO_CELLS; ++g) {
                 if ((unsigned)g >= m && (unsigned)g < avail) S.fifo[lane][g - m] = make_uint2(kg[g], ng[g]);
