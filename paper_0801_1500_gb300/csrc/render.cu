@@ -688,9 +688,11 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
             unsigned qn = 0;
             for (unsigned base = 0; base < T; base += 32) {
                 // rays mark where their pairs start inside this chunk; a pair's
-                // ray is the last start at or before it
-                const bool mine = cnt > 0 && ex < base + 32 && ex + cnt > base;
-                const unsigned pos = ex > base ? ex - base : 0u;
+                // ray is the last start at or before it. A ray takes part when its
+                // pairs [ex, incl) are not empty and meet [base, base + 32).
+                const unsigned u = ex > base ? ex : base;
+                const unsigned pos = u - base;
+                const bool mine = pos < 32u && incl > u;
                 if (mine) S.owner[pos] = (uint32_t)lane;
                 const unsigned starts = __reduce_or_sync(FULL, mine ? (1u << pos) : 0u);
                 __syncwarp();
@@ -723,12 +725,14 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
                     const AoRay<R> ray = S.ray[r];
                     R t;
                     const bool hit = hit_object<R>(ao_obj(S, r, uobj), id, ray.o, ray.d, R(0), ray.tmax, t);
-                    hitbits |= __reduce_or_sync(FULL, hit ? (1u << r) : 0u);
+                    hitbits |= hit ? (1u << r) : 0u;  // OR-ed over the warp after the last chunk
                     __syncwarp();
                 }
             }
             if constexpr (AoCfg<R>::queue) {
                 if (qn > 0) hitbits |= ao_test_batch(S, lane, qn, uobj);
+            } else {
+                hitbits = __reduce_or_sync(FULL, hitbits);
             }
         }
         // 5. any hit occludes the ray; a ray whose walk ended escapes
