@@ -105,7 +105,8 @@ def committed_profile(workload_name, precision):
     if kv.get("sources_hash") != sources_hash():
         return {}
     out = {}
-    for key in ("dram_bytes_per_launch", "issue_active_pct"):
+    for key in ("dram_bytes_per_launch", "issue_active_pct", "warp_instructions_per_launch", "grid_lambda",
+                "refill", "block"):
         try:
             out[key] = float(kv[key])
         except (KeyError, ValueError):
@@ -809,6 +810,23 @@ def main():
                            "unit": "GB/s", "frac": round(l2_gbs / calib["l2_read_gbs"], 4),
                            "bytes_per_ray": round(bpr, 1),
                            "peak_source": "16-byte reads of a buffer of half the L2 (gbrt_microbench, this GPU)"}}
+            tun = G.gbrt_get_tuning(r.ctx)
+            if ("warp_instructions_per_launch" in prof and prof.get("grid_lambda") == lam
+                    and prof.get("refill") == tun["refill"] and prof.get("block") == tun["block"]):
+                # the instruction-issue bound: ncu's warp instructions of one
+                # launch (same kernel sources and launch shape) over the live
+                # kernel time, against one instruction a clock per scheduler
+                inst = prof["warp_instructions_per_launch"]
+                issue_peak = 4 * props.multi_processor_count * sm_max * 1e6 / 1e9
+                issue = inst / ao_s / 1e9
+                roof["issue"] = {"bound": "issue", "achieved": round(issue, 1), "peak": round(issue_peak, 1),
+                                 "unit": "G warp instructions/s", "frac": round(issue / issue_peak, 4),
+                                 "warp_instructions_per_launch": int(inst),
+                                 "warp_instructions_per_ao_ray": round(inst / ao_rays, 2),
+                                 "peak_source": f"4 warp schedulers x {props.multi_processor_count} SMs x "
+                                                f"{sm_max:.0f} MHz",
+                                 "count_source": "ncu smsp__inst_executed.sum from the committed summary of this "
+                                                 "kernel, workload and launch shape"}
             fp64 = extras.get("fp64_path_1.1MP")
             if fp64 and "phases_ms" in fp64:
                 # the plain FP64 path's AO walk against the FP64 FMA rate measured
