@@ -76,6 +76,87 @@ __device__ __forceinline__ V3<float> view_dir_f(const FrameDev& f, uint32_t q) {
     return rsqrtf(dot(d, d)) * d;
 }
 
+// Float-float arithmetic (Dekker 1971, Knuth's TwoSum): a value held as an
+// unevaluated sum hi + lo of two floats, about 48 bits. The float path forms
+// its primary ray and the two points it rounds from that ray this way, on the
+// FP32 pipe, instead of in FP64 (a GB300 SM runs FP64 at 1/64 of the FP32
+// rate). Products and sums use the _rn intrinsics so that no step is fused.
+struct Ff3 {
+    V3<float> hi, lo;
+};
+
+// s + e = a + b exactly (s the rounded sum)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// round(x + t d - p), one component: x and d float pairs, t and p floats
+__device__ __forceinline__ float ff_point(float xh, float xl, float t, float dh, float dl, float p) {
+    float s1, e1, s2, e2;
+    two_sum(xh, -p, s1, e1);
+    const float pr = __fmul_rn(t, dh);
+    const float ep = __fmaf_rn(t, dh, -pr);  // t dh - pr exactly
+    two_sum(s1, pr, s2, e2);
+    return __fadd_rn(s2, __fadd_rn(__fadd_rn(xl, e1), __fadd_rn(__fadd_rn(e2, ep), __fmul_rn(t, dl))));
+}
+
+// x + t d - p rounded to float, per component
+__device__ __forceinline__ V3<float> ff_point3(const Ff3& x, float t, const Ff3& d, V3<float> p) {
+    return v3(ff_point(x.hi.x, x.lo.x, t, d.hi.x, d.lo.x, p.x), ff_point(x.hi.y, x.lo.y, t, d.hi.y, d.lo.y, p.y),
+              ff_point(x.hi.z, x.lo.z, t, d.hi.z, d.lo.z, p.z));
+}
+
+// round(x + t d) and what the rounding left out (x + t d = point + rest to
+// about 2^-48 of the point), one component
+__device__ __forceinline__ float ff_entry(float xh, float xl, float t, float dh, float dl, float& rest) {
+    const float pr = __fmul_rn(t, dh);
+    const float ep = __fmaf_rn(t, dh, -pr);
+    float s, e;
+    two_sum(xh, pr, s, e);
+    const float l = __fadd_rn(__fadd_rn(xl, e), __fadd_rn(ep, __fmul_rn(t, dl)));
+    const float pt = __fadd_rn(s, l);
+    rest = __fsub_rn(l, __fsub_rn(pt, s));
+    return pt;
+}
+
+// a0 + i ai + j aj as a float pair (i, j below 2^24, so i ai_hi and j aj_hi
+// are split exactly by an FMA)
+__device__ __forceinline__ void ff_affine(float a0h, float a0l, float fi, float aih, float ail, float fj, float ajh,
+                                          float ajl, float& hi, float& lo) {
+    const float p1 = __fmul_rn(fi, aih), e1 = __fmaf_rn(fi, aih, -p1);
+    const float p2 = __fmul_rn(fj, ajh), e2 = __fmaf_rn(fj, ajh, -p2);
+    float s1, r1, s2, r2;
+    two_sum(a0h, p1, s1, r1);
+    two_sum(s1, p2, s2, r2);
+    const float l = __fadd_rn(__fadd_rn(__fadd_rn(a0l, __fmul_rn(fi, ail)), __fadd_rn(e1, e2)),
+                              __fadd_rn(__fadd_rn(r1, r2), __fmul_rn(fj, ajl)));
+    hi = __fadd_rn(s2, l);  // |l| is far below |s2|: a fast two-sum renormalises
+    lo = __fsub_rn(l, __fsub_rn(hi, s2));
+}
+
+// The float path's primary ray of pixel (i, j) as float pairs. Orthographic:
+// the origin is affine in (i, j) and the direction fixed, so no FP64 is left;
+// pinhole: the origin is the eye and the direction comes from the FP64 ray.
+__device__ __forceinline__ void primary_ray_ff(const FrameDev& f, int i, int j, Ff3& o, Ff3& d) {
+    if (f.cam_kind == GBRT_CAMERA_ORTHO) {
+        const float fi = (float)i, fj = (float)j;
+        ff_affine(f.o00_hi[0], f.o00_lo[0], fi, f.si_hi[0], f.si_lo[0], fj, f.sj_hi[0], f.sj_lo[0], o.hi.x, o.lo.x);
+        ff_affine(f.o00_hi[1], f.o00_lo[1], fi, f.si_hi[1], f.si_lo[1], fj, f.sj_hi[1], f.sj_lo[1], o.hi.y, o.lo.y);
+        ff_affine(f.o00_hi[2], f.o00_lo[2], fi, f.si_hi[2], f.si_lo[2], fj, f.sj_hi[2], f.sj_lo[2], o.hi.z, o.lo.z);
+        d.hi = v3(f.dir_hi[0], f.dir_hi[1], f.dir_hi[2]);
+        d.lo = v3(f.dir_lo[0], f.dir_lo[1], f.dir_lo[2]);
+    } else {
+        V3<double> o64, d64;
+        primary_ray64(f, i, j, o64, d64);
+        o.hi = v3(f.eye_hi[0], f.eye_hi[1], f.eye_hi[2]);
+        o.lo = v3(f.eye_lo[0], f.eye_lo[1], f.eye_lo[2]);
+        d.hi = to_f(d64);
+        d.lo = to_f(d64 - to_d(d.hi));
+    }
+}
+
 // Refinement of an FP32 root in the object's own frame. The FP32 walk's root t
 // (along the FP64 ray o + t d) is turned into the hit's offset from the
 // object's base point p0 -- one FP64 point o + t d - p0, rounded to FP32; it
@@ -83,22 +164,25 @@ __device__ __forceinline__ V3<float> view_dir_f(const FrameDev& f, uint32_t q) {
 // that -- and Newton steps in FP32 then move it along the ray by s to the
 // surface: F(s) = |w_p + s d_p|^2 - r^2 (w_p, d_p: the parts perpendicular to
 // the axis a; all of w and d for a sphere). The result is the offset w + s d
-// (the re-projection then needs no FP64 at all) and the root t + s in FP64
-// for ranking near-ties. False when the steps do not settle (a grazing ray):
-// the offset then stays at the FP32 root's point.
+// (the re-projection then needs no FP64 at all) and the root t + s, exactly,
+// as a float pair for ranking near-ties. False when the steps do not settle (a
+// grazing ray): the offset then stays at the FP32 root's point. The point is
+// formed from the ray's float pairs (p0 is a float: the scene's coordinates
+// are), accurate to far below the float it is rounded to.
 struct LocalHit {
-    V3<float> w;  // hit point - p0
-    double t;     // root along the FP64 ray
+    V3<float> w;     // hit point - p0
+    float t, t_lo;   // root along the ray from its grid entry: t + t_lo exactly
 };
 
-__device__ __forceinline__ bool local_root(const SceneDev& sc, uint32_t id, V3<double> o, V3<double> d,
-                                           V3<float> df, double t, LocalHit& lh) {
-    const double2* q = sc.obj64 + 4 * (size_t)id;
-    const double2 q0 = __ldg(q), q1 = __ldg(q + 1);
+// x = (oe, rest): the ray's grid-entry point and what its rounding left out;
+// t: the FP32 root measured from oe along d (d.hi: the walk's direction)
+__device__ __forceinline__ bool local_root(const SceneDev& sc, uint32_t id, const Ff3& x, const Ff3& d, float t,
+                                           LocalHit& lh) {
+    const V3<float> df = d.hi;
     V3<float> p0f, a;
     float L, r;
     Obj<float>::load(sc.obj, id, p0f, a, L, r);
-    const V3<float> w = to_f(madd(o, t, d) - v3(q0.x, q0.y, q1.x));
+    const V3<float> w = ff_point3(x, t, d, p0f);
     const float wa = dot(w, a), da = dot(df, a);
     const V3<float> wp = madd(w, -wa, a), dp = madd(df, -da, a);
     const float A = dot(dp, dp), B = dot(wp, dp), C = fmaf(-r, r, dot(wp, wp));
@@ -112,7 +196,7 @@ __device__ __forceinline__ bool local_root(const SceneDev& sc, uint32_t id, V3<d
     const bool ok = fabsf(corr) <= 1e-4f * (fabsf(s) + r) && isfinite(s);
     if (!ok) s = 0.0f;
     lh.w = madd(w, s, df);
-    lh.t = t + (double)s;
+    two_sum(t, s, lh.t, lh.t_lo);
     return ok;
 }
 
@@ -120,21 +204,44 @@ __device__ __forceinline__ bool local_root(const SceneDev& sc, uint32_t id, V3<d
 // (one FP64 point rounded once, so coordinates stay small relative to the
 // scene), then the winner -- and a runner-up within a relative 1e-4 band --
 // refined in its object's frame (local_root); the nearer refined root wins.
-__device__ __forceinline__ bool nearest_fp32_refined(const FrameDev& f, V3<double> o64, V3<double> d64,
-                                                     V3<float> df, uint32_t& id, LocalHit& lh, bool& overflow) {
+// The ray's grid-entry point at te0, rounded once (x.hi), and what the
+// rounding left out (x.lo).
+__device__ __forceinline__ void entry_point(const Ff3& o, const Ff3& d, float te0, Ff3& x) {
+    x.hi.x = ff_entry(o.hi.x, o.lo.x, te0, d.hi.x, d.lo.x, x.lo.x);
+    x.hi.y = ff_entry(o.hi.y, o.lo.y, te0, d.hi.y, d.lo.y, x.lo.y);
+    x.hi.z = ff_entry(o.hi.z, o.lo.z, te0, d.hi.z, d.lo.z, x.lo.z);
+}
+
+__device__ __forceinline__ bool nearest_fp32_refined(const FrameDev& f, int i, int j, uint32_t& id, LocalHit& lh,
+                                                     bool& overflow) {
     const float inf = Num<float>::inf();
-    V3<float> of = to_f(o64);
+    Ff3 o, d, x;
+    primary_ray_ff(f, i, j, o, d);
     float te0, te1;
-    if (!clip_grid<float>(f.grid, of, df, 0.0f, inf, te0, te1)) return false;
-    V3<float> oe = to_f(madd(o64, (double)te0, d64));
+    if (!clip_grid<float>(f.grid, o.hi, d.hi, 0.0f, inf, te0, te1)) return false;
+    // the walk starts at the entry point rounded once
+    entry_point(o, d, te0, x);
     Nearest<float> h;
-    if (!trace_nearest<float>(f.grid, f.scene, oe, df, 0.0f, inf, h, overflow)) return false;
-    local_root(f.scene, h.id1, o64, d64, df, (double)(te0 + h.t1), lh);
+    if (!trace_nearest<float>(f.grid, f.scene, x.hi, d.hi, 0.0f, inf, h, overflow)) return false;
+    // the refinement needs what the rounding left out: the ray and its entry
+    // point are formed again (the same steps give the same floats), which is
+    // cheaper than holding their low parts in registers through the walk
+    // (the copies of i and j keep the compiler from reusing the first ones)
+    int i2, j2;
+    asm volatile("mov.b32 %0, %1;" : "=r"(i2) : "r"(i));
+    asm volatile("mov.b32 %0, %1;" : "=r"(j2) : "r"(j));
+    primary_ray_ff(f, i2, j2, o, d);
+    entry_point(o, d, te0, x);
+    local_root(f.scene, h.id1, x, d, h.t1, lh);
     id = h.id1;
     if (h.id2 != GBRT_MISS && (h.t2 - h.t1) <= 1e-4f * (h.t1 + te0)) {
         LocalHit l2;
-        local_root(f.scene, h.id2, o64, d64, df, (double)(te0 + h.t2), l2);
-        if (l2.t < lh.t || (l2.t == lh.t && h.id2 < h.id1)) {
+        local_root(f.scene, h.id2, x, d, h.t2, l2);
+        // t + t_lo pairs are normalised, so comparing them in order compares
+        // the exact roots
+        const bool nearer = l2.t < lh.t || (l2.t == lh.t && l2.t_lo < lh.t_lo);
+        const bool same = l2.t == lh.t && l2.t_lo == lh.t_lo;
+        if (nearer || (same && h.id2 < h.id1)) {
             id = h.id2;
             lh = l2;
         }
@@ -245,11 +352,10 @@ __global__ void __launch_bounds__(256) k_primary(const __grid_constant__ BatchDe
         LocalHit lh;
         bool hit = false;
         if (inside) {
-            primary_ray64(F, i, j, o64, d64);
             if (MODE == GBRT_FP32) {
-                hit = nearest_fp32_refined(F, o64, d64, view_dir_f(F, (uint32_t)j * (uint32_t)F.W + (uint32_t)i),
-                                           id, lh, overflow);
+                hit = nearest_fp32_refined(F, i, j, id, lh, overflow);
             } else {
+                primary_ray64(F, i, j, o64, d64);
                 Nearest<double> h;
                 hit = trace_nearest<double>(F.grid, F.scene, o64, d64, 0.0, Num<double>::inf(), h, overflow);
                 id = h.id1;
