@@ -85,19 +85,22 @@ FrameDev make_frame(const gbrt_scene* scene, const gbrt_grid* grid, const gbrt_c
     f.inv_w_f = (float)f.inv_w;
     f.inv_h_f = (float)f.inv_h;
     {
-        // orthographic origin of pixel (i, j): eye + u right + v up with
+        // pixel (i, j) sits at u right + v up from the view axis with
         // u = half_w ((2i + 1)/W - 1) = a_u i + b_u and v = half_h (1 - (2j + 1)/H)
-        // = a_v j + b_v, i.e. o00 + i si + j sj; each split into a float pair
+        // = a_v j + b_v: the orthographic origin eye + u right + v up and the
+        // pinhole direction dir_unit + u right + v up (before normalisation)
+        // are a0 + i ai + j aj; each vector split into float pairs
         const double a_u = 2.0 * f.half_w * f.inv_w, b_u = f.half_w * (f.inv_w - 1.0);
         const double a_v = -2.0 * f.half_h * f.inv_h, b_v = f.half_h * (1.0 - f.inv_h);
         auto split = [](double x, float& hi, float& lo) {
             hi = (float)x;
             lo = (float)(x - (double)hi);
         };
+        const double* base = cam->kind == GBRT_CAMERA_ORTHO ? f.eye : f.dir_unit;
         for (int k = 0; k < 3; ++k) {
-            split(f.eye[k] + b_u * f.right[k] + b_v * f.up[k], f.o00_hi[k], f.o00_lo[k]);
-            split(a_u * f.right[k], f.si_hi[k], f.si_lo[k]);
-            split(a_v * f.up[k], f.sj_hi[k], f.sj_lo[k]);
+            split(base[k] + b_u * f.right[k] + b_v * f.up[k], f.a0_hi[k], f.a0_lo[k]);
+            split(a_u * f.right[k], f.ai_hi[k], f.ai_lo[k]);
+            split(a_v * f.up[k], f.aj_hi[k], f.aj_lo[k]);
             split(f.dir_unit[k], f.dir_hi[k], f.dir_lo[k]);
             split(f.eye[k], f.eye_hi[k], f.eye_lo[k]);
         }

@@ -62,9 +62,10 @@ struct FrameDev {
     float dir_f[3], up_f[3], right_f[3];
     float half_w_f, half_h_f, inv_w_f, inv_h_f;
     // the float path's primary rays as float-float pairs (value = hi + lo,
-    // |lo| <= half an ulp of hi): the orthographic origin of pixel (i, j) is
-    // o00 + i si + j sj, the direction dir_unit; the pinhole origin is eye
-    float o00_hi[3], o00_lo[3], si_hi[3], si_lo[3], sj_hi[3], sj_lo[3];
+    // |lo| <= half an ulp of hi). The part that varies with pixel (i, j) is
+    // affine in it, a0 + i ai + j aj: the orthographic origin (direction
+    // dir_unit), or the pinhole direction before normalisation (origin eye)
+    float a0_hi[3], a0_lo[3], ai_hi[3], ai_lo[3], aj_hi[3], aj_lo[3];
     float dir_hi[3], dir_lo[3], eye_hi[3], eye_lo[3];
     int32_t cam_kind;
     int32_t W, H, spp;

@@ -136,24 +136,66 @@ __device__ __forceinline__ void ff_affine(float a0h, float a0l, float fi, float 
     lo = __fsub_rn(l, __fsub_rn(hi, s2));
 }
 
-// The float path's primary ray of pixel (i, j) as float pairs. Orthographic:
-// the origin is affine in (i, j) and the direction fixed, so no FP64 is left;
-// pinhole: the origin is the eye and the direction comes from the FP64 ray.
+// a.hi + a.lo times b.hi + b.lo, as a pair (the lo * lo term dropped)
+__device__ __forceinline__ void ff_mul(float ah, float al, float bh, float bl, float& hi, float& lo) {
+    const float p = __fmul_rn(ah, bh);
+    const float e = __fadd_rn(__fmaf_rn(ah, bh, -p), __fadd_rn(__fmul_rn(ah, bl), __fmul_rn(al, bh)));
+    hi = __fadd_rn(p, e);
+    lo = __fsub_rn(e, __fsub_rn(hi, p));
+}
+
+// q / |q| as float pairs. 1/|q| starts from the hardware rsqrtf of |q|^2's
+// high part and takes one Newton-Raphson step for the reciprocal square root,
+// y1 = y0 + y0 (1 - n y0^2) / 2, with the residual 1 - n y0^2 formed from
+// exact products; the step leaves about twice the seed's bits.
+__device__ __forceinline__ void ff_normalise(Ff3& q) {
+    float n, ne;  // |q|^2 = n + ne
+    {
+        float sq, se;
+        ff_mul(q.hi.x, q.lo.x, q.hi.x, q.lo.x, n, ne);
+        ff_mul(q.hi.y, q.lo.y, q.hi.y, q.lo.y, sq, se);
+        float s, e;
+        two_sum(n, sq, s, e);
+        n = s;
+        ne = __fadd_rn(__fadd_rn(ne, se), e);
+        ff_mul(q.hi.z, q.lo.z, q.hi.z, q.lo.z, sq, se);
+        two_sum(n, sq, s, e);
+        n = s;
+        ne = __fadd_rn(__fadd_rn(ne, se), e);
+    }
+    const float y0 = rsqrtf(n);
+    float a, b;  // y0^2 = a + b exactly
+    a = __fmul_rn(y0, y0);
+    b = __fmaf_rn(y0, y0, -a);
+    float c, cd;  // n a = c + cd exactly
+    c = __fmul_rn(n, a);
+    cd = __fmaf_rn(n, a, -c);
+    // 1 - (n + ne)(a + b); 1 - c is exact (c is within a few ulp of 1)
+    const float r = __fsub_rn(__fsub_rn(__fsub_rn(1.0f, c), cd), __fadd_rn(__fmul_rn(n, b), __fmul_rn(ne, a)));
+    const float yl = __fmul_rn(__fmul_rn(0.5f, y0), r);
+    ff_mul(q.hi.x, q.lo.x, y0, yl, q.hi.x, q.lo.x);
+    ff_mul(q.hi.y, q.lo.y, y0, yl, q.hi.y, q.lo.y);
+    ff_mul(q.hi.z, q.lo.z, y0, yl, q.hi.z, q.lo.z);
+}
+
+// The float path's primary ray of pixel (i, j) as float pairs, with no FP64:
+// the orthographic origin, or the pinhole direction before normalisation, is
+// affine in (i, j).
 __device__ __forceinline__ void primary_ray_ff(const FrameDev& f, int i, int j, Ff3& o, Ff3& d) {
+    const float fi = (float)i, fj = (float)j;
+    Ff3 v;
+    ff_affine(f.a0_hi[0], f.a0_lo[0], fi, f.ai_hi[0], f.ai_lo[0], fj, f.aj_hi[0], f.aj_lo[0], v.hi.x, v.lo.x);
+    ff_affine(f.a0_hi[1], f.a0_lo[1], fi, f.ai_hi[1], f.ai_lo[1], fj, f.aj_hi[1], f.aj_lo[1], v.hi.y, v.lo.y);
+    ff_affine(f.a0_hi[2], f.a0_lo[2], fi, f.ai_hi[2], f.ai_lo[2], fj, f.aj_hi[2], f.aj_lo[2], v.hi.z, v.lo.z);
     if (f.cam_kind == GBRT_CAMERA_ORTHO) {
-        const float fi = (float)i, fj = (float)j;
-        ff_affine(f.o00_hi[0], f.o00_lo[0], fi, f.si_hi[0], f.si_lo[0], fj, f.sj_hi[0], f.sj_lo[0], o.hi.x, o.lo.x);
-        ff_affine(f.o00_hi[1], f.o00_lo[1], fi, f.si_hi[1], f.si_lo[1], fj, f.sj_hi[1], f.sj_lo[1], o.hi.y, o.lo.y);
-        ff_affine(f.o00_hi[2], f.o00_lo[2], fi, f.si_hi[2], f.si_lo[2], fj, f.sj_hi[2], f.sj_lo[2], o.hi.z, o.lo.z);
+        o = v;
         d.hi = v3(f.dir_hi[0], f.dir_hi[1], f.dir_hi[2]);
         d.lo = v3(f.dir_lo[0], f.dir_lo[1], f.dir_lo[2]);
     } else {
-        V3<double> o64, d64;
-        primary_ray64(f, i, j, o64, d64);
         o.hi = v3(f.eye_hi[0], f.eye_hi[1], f.eye_hi[2]);
         o.lo = v3(f.eye_lo[0], f.eye_lo[1], f.eye_lo[2]);
-        d.hi = to_f(d64);
-        d.lo = to_f(d64 - to_d(d.hi));
+        ff_normalise(v);
+        d = v;
     }
 }
 
