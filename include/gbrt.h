@@ -356,9 +356,9 @@ GBRT_API int gbrt_philox4x32_10(gbrt_ctx* ctx, const uint32_t* ctr, const uint32
  *    larger frames are rejected with GBRT_EINVAL, as are host output
  *    pointers (params->out_flags must be 0) and supersampling
  *    (camera->aa > 1).
- *  - The first call on a device does that device's set-up (it looks up the
- *    array's device address and configures the kernels); make that first
- *    call before any stream capture.
+ *  - The first call on a device does that device's set-up: it looks up the
+ *    array's device address and configures the kernels, both synchronous
+ *    runtime calls.
  *  - All calls share the one array and it keeps the last call's contents;
  *    the call clears what must start at zero. Calls whose work overlaps on
  *    the GPU (different streams, or different host threads) race on it:
