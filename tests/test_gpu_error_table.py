@@ -2,9 +2,9 @@
 
 One row per (workload, precision): the small globule at 256x256 (8 spp), the
 paper-sized scene at 965x1137 (16 spp, every pixel), the 256x256 centre crop
-of its 3860x4548 frame, one orbit frame of each orbit size (512x512,
-965x1137, 1920x1080, 8-32 spp), and the smallest and largest scenes of the
-serving set (1k and 250k objects). Each row meets the parity rule; the table
+of its 3860x4548 frame, a pinhole view of it, one orbit frame of each orbit
+size (512x512, 965x1137, 1920x1080, 8-32 spp), and the smallest and largest
+scenes of the serving set (1k and 250k objects). Each row meets the parity rule; the table
 (non-grazing id mismatches, grazing pixels, fraction of pixels beyond 1/255,
 mean and largest absolute error, AO counts equal) is printed, and written as
 JSON where GBRT_ERROR_TABLE names a file.
@@ -98,6 +98,16 @@ def test_paper_scene_17mp_crop(G, R, oracle, paper, prec):
     p = S.Params(ao_samples=16, seed=0, precision=prec)
     measure(G, R, oracle, "paper-sized, 17.6 MP frame, 256x256 centre crop", paper, S.ortho_camera(paper, W, H),
             W, H, p, pixels=(jj * W + ii).ravel())
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_paper_scene_pinhole(G, R, oracle, paper, prec):
+    # the pinhole ray's direction is normalised per pixel (float-float in the
+    # FP32 path); eye outside the globule, 30 degree field, every pixel
+    W, H = 965, 1137
+    p = S.Params(ao_samples=16, seed=0, precision=prec)
+    measure(G, R, oracle, "paper-sized, pinhole 30 deg", paper, S.pinhole_camera(paper, W, H, angle_deg=20.0,
+                                                                                  fov_deg=30.0), W, H, p)
 
 
 @pytest.mark.parametrize("size", [(512, 512), (965, 1137), (1920, 1080)])
