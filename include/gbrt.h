@@ -62,7 +62,7 @@ extern "C" {
 #define GBRT_BATCH_GRAPH 2    /* gbrt_render_batch: replay through a CUDA graph */
 
 /* ---- precision ---- */
-#define GBRT_FP32 0  /* FP32 traversal, intersection and shading; FP64 ray, hit refined in its object's frame */
+#define GBRT_FP32 0  /* FP32 traversal, intersection and shading; float-float ray, hit refined in its object's frame */
 #define GBRT_FP64 1  /* FP64 throughout (the paper's all-double-precision build, Sec. 2) */
 
 #define GBRT_CAMERA_ORTHO 0

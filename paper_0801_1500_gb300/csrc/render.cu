@@ -200,17 +200,17 @@ __device__ __forceinline__ void primary_ray_ff(const FrameDev& f, int i, int j, 
 }
 
 // Refinement of an FP32 root in the object's own frame. The FP32 walk's root t
-// (along the FP64 ray o + t d) is turned into the hit's offset from the
-// object's base point p0 -- one FP64 point o + t d - p0, rounded to FP32; it
-// has the size of the object (|w| <= r + L), so FP32 holds it to ~1e-7 of
-// that -- and Newton steps in FP32 then move it along the ray by s to the
-// surface: F(s) = |w_p + s d_p|^2 - r^2 (w_p, d_p: the parts perpendicular to
-// the axis a; all of w and d for a sphere). The result is the offset w + s d
-// (the re-projection then needs no FP64 at all) and the root t + s, exactly,
-// as a float pair for ranking near-ties. False when the steps do not settle (a
-// grazing ray): the offset then stays at the FP32 root's point. The point is
-// formed from the ray's float pairs (p0 is a float: the scene's coordinates
-// are), accurate to far below the float it is rounded to.
+// (along the ray x + t d, x its grid-entry point) is turned into the hit's
+// offset from the object's base point p0 -- the point x + t d - p0 formed from
+// float pairs (p0 is a float: the scene's coordinates are) and rounded to
+// FP32; it has the size of the object (|w| <= r + L), so FP32 holds it to
+// ~1e-7 of that -- and Newton steps in FP32 then move it along the ray by s to
+// the surface: F(s) = |w_p + s d_p|^2 - r^2 (w_p, d_p: the parts perpendicular
+// to the axis a; all of w and d for a sphere). The result is the offset w + s d
+// (the re-projection then needs no more precision than FP32) and the root
+// t + s, exactly, as a float pair for ranking near-ties. False when the steps
+// do not settle (a grazing ray): the offset then stays at the FP32 root's
+// point.
 struct LocalHit {
     V3<float> w;     // hit point - p0
     float t, t_lo;   // root along the ray from its grid entry: t + t_lo exactly
@@ -242,10 +242,6 @@ __device__ __forceinline__ bool local_root(const SceneDev& sc, uint32_t id, cons
     return ok;
 }
 
-// FP32 path: nearest hit in FP32 from the FP32 ray re-based at the grid entry
-// (one FP64 point rounded once, so coordinates stay small relative to the
-// scene), then the winner -- and a runner-up within a relative 1e-4 band --
-// refined in its object's frame (local_root); the nearer refined root wins.
 // The ray's grid-entry point at te0, rounded once (x.hi), and what the
 // rounding left out (x.lo).
 __device__ __forceinline__ void entry_point(const Ff3& o, const Ff3& d, float te0, Ff3& x) {
@@ -254,6 +250,10 @@ __device__ __forceinline__ void entry_point(const Ff3& o, const Ff3& d, float te
     x.hi.z = ff_entry(o.hi.z, o.lo.z, te0, d.hi.z, d.lo.z, x.lo.z);
 }
 
+// FP32 path: nearest hit in FP32 from the float-float ray re-based at its
+// grid entry (one rounding, so coordinates stay small relative to the scene),
+// then the winner -- and a runner-up within a relative 1e-4 band -- refined in
+// its object's frame (local_root); the nearer refined root wins.
 __device__ __forceinline__ bool nearest_fp32_refined(const FrameDev& f, int i, int j, uint32_t& id, LocalHit& lh,
                                                      bool& overflow) {
     const float inf = Num<float>::inf();
