@@ -4,13 +4,23 @@ Render requests (scene, camera, resolution, AO samples, precision) arrive at
 any time. A request is admitted when its device footprint -- its output
 buffers -- fits in the free part of the HBM budget; a request larger than the
 whole budget is rejected. Admitted requests are cut into bands of rows. The
-loop forms waves: each wave takes the next band of every admitted request in
-turn (oldest first) until the wave's ray budget is full, and renders the wave
-as ONE batched launch sequence (``gbrt_render_batch``), so the bands of
-different requests share the GPU. A request that arrives while waves are
-running joins the next wave; it does not wait for earlier requests to finish.
-A band keeps its whole-image pixel coordinates and sample counters, so every
-result is the same whether its request ran alone or in a mix.
+loop forms waves and renders each as ONE batched launch sequence
+(``gbrt_render_batch``), so the bands of different requests share the GPU. A
+wave takes admitted requests in order of their estimated remaining GPU time,
+less ``aging`` times the time they have waited (shortest remaining work
+first, with waiting time counted in so that no request waits without bound:
+a request of T seconds of work gets ahead of fresh small ones after about
+T / aging seconds), and gives each all its remaining bands while the wave's
+ray and pixel budgets last. A request that arrives while waves are running
+joins the next wave; it does not wait for earlier requests to finish. A band
+keeps its whole-image pixel coordinates and sample counters, so every result
+is the same whether its request ran alone or in a mix.
+
+On the serving trace (8 scenes, 4 resolutions, 4-64 spp, Poisson arrivals)
+this order lowers the median latency at 100 requests/s about fourfold and the
+99th percentile by about a quarter against taking one band of every request
+in arrival order, per wave, in a simulation of the loop calibrated on that
+order's measured latencies.
 
 The scheduler talks to a backend with four calls (upload, allocate outputs,
 launch a wave, wait for a wave), so its host logic runs under a fake backend
@@ -78,11 +88,17 @@ class Server:
     wave_pixels   pixels per wave (bounds the library's per-wave working memory)
     band_rows     rows per band
     max_inflight  waves enqueued ahead of the oldest unfinished one
+    rays_per_s    the GPU's ray rate, to turn a request's remaining rays into
+                  time (its order of magnitude is what matters)
+    aging         seconds of priority a request gains per second it waits
     """
 
     def __init__(self, backend, scenes, hbm_budget: int = 8 << 30, wave_rays: float = 48e6,
-                 wave_pixels: int = 4 << 20, band_rows: int = 64, max_inflight: int = 2):
+                 wave_pixels: int = 4 << 20, band_rows: int = 64, max_inflight: int = 2,
+                 rays_per_s: float = 1e10, aging: float = 0.1):
         self.b = backend
+        self.rays_per_s = float(rays_per_s)
+        self.aging = float(aging)
         self.handles = [self.b.upload(sc) for sc in scenes]
         self.hbm_budget = int(hbm_budget)
         self.wave_rays = float(wave_rays)
@@ -145,17 +161,20 @@ class Server:
             self.used += req.footprint()
             self.active.append(req)
 
-    def _build_wave(self) -> List[Band]:
-        """Round-robin bands over admitted requests, oldest first, within the budgets."""
+    def priority(self, req: Request, now: float) -> float:
+        """Estimated remaining GPU seconds less aging x seconds waited (lower
+        goes first)."""
+        return req.est_rays(req.height - req.rows_issued) / self.rays_per_s - self.aging * (now - req.t_submit)
+
+    def _build_wave(self, now: Optional[float] = None) -> List[Band]:
+        """Bands of the admitted requests in priority order, each request's
+        remaining bands in turn, within the wave's budgets."""
+        now = time.perf_counter() if now is None else now
         bands: List[Band] = []
         rays = 0.0
         pixels = 0
-        progress = True
-        while progress:
-            progress = False
-            for req in self.active:
-                if req.rows_issued >= req.height:
-                    continue
+        for req in sorted(self.active, key=lambda r: self.priority(r, now)):
+            while req.rows_issued < req.height:
                 r0 = req.rows_issued
                 r1 = min(req.height, r0 + self.band_rows)
                 est = req.est_rays(r1 - r0)
@@ -166,7 +185,6 @@ class Server:
                 req.rows_issued = r1
                 rays += est
                 pixels += px
-                progress = True
         return bands
 
     def _retire(self, bands: List[Band]):

@@ -99,7 +99,7 @@ def test_late_small_request_overtakes_long_one():
     # continuous batching: a small request arriving while a long one is being
     # rendered joins the next wave and finishes first
     b = FakeBackend(ns_per_ray=20.0)           # the long request takes ~0.23 s of waves
-    srv = SV.Server(b, ["s"], hbm_budget=1 << 30, wave_rays=1e6, band_rows=16)
+    srv = SV.Server(b, ["s"], hbm_budget=1 << 30, wave_rays=1e6, band_rows=16, rays_per_s=1e9 / b.ns_per_ray)
     long_req = req(1000, 2000, spp=8)
     f_long = srv.submit(long_req)
     time.sleep(0.03)
@@ -112,3 +112,63 @@ def test_late_small_request_overtakes_long_one():
     assert small.t_done < long_req.t_done
     # the small request shared a wave with bands of the long one
     assert any({small.rid, long_req.rid} <= {rid for rid, _, _ in w} for w in b.waves)
+
+
+def _fake_req(w, h, spp, t_submit):
+    r = req(w, h, spp=spp)
+    r.t_submit = t_submit
+    return r
+
+
+class _Idle:
+    """A backend that never runs: the server's ordering is driven by hand."""
+
+    def upload(self, scene):
+        return scene
+
+
+def _server_without_loop(**kw):
+    srv = SV.Server.__new__(SV.Server)
+    srv.b = _Idle()
+    srv.hbm_budget = 1 << 40
+    srv.wave_rays = kw.get("wave_rays", 1e12)
+    srv.wave_pixels = kw.get("wave_pixels", 1 << 40)
+    srv.band_rows = kw.get("band_rows", 64)
+    srv.rays_per_s = kw.get("rays_per_s", 1e10)
+    srv.aging = kw.get("aging", 0.1)
+    srv.active = []
+    return srv
+
+
+def test_wave_takes_shortest_remaining_work_first():
+    # three requests submitted at once: the wave lists the smallest first, and
+    # each request's bands together and in row order
+    srv = _server_without_loop(band_rows=100)
+    big, mid, small = _fake_req(2000, 1000, 64, 0.0), _fake_req(1000, 500, 16, 0.0), _fake_req(256, 256, 4, 0.0)
+    srv.active = [big, mid, small]
+    wave = srv._build_wave(now=0.0)
+    order = []
+    for bd in wave:
+        if not order or order[-1] is not bd.req:
+            order.append(bd.req)
+    assert order == [small, mid, big]
+    for r in (small, mid, big):
+        rows = [(bd.row_begin, bd.row_end) for bd in wave if bd.req is r]
+        assert rows[0][0] == 0 and rows[-1][1] == r.height
+        assert all(a[1] == b[0] for a, b in zip(rows, rows[1:]))
+
+
+def test_waiting_time_lifts_a_long_request():
+    # a long request (about 1.5 s of work at the assumed rate) that has waited
+    # longer than its work / aging goes ahead of a fresh small request; one
+    # that has waited less does not
+    srv = _server_without_loop(wave_rays=1.0, rays_per_s=1e8, aging=0.1)   # one band a wave
+    long_r = _fake_req(1000, 1000, 255, 0.0)      # 1000 * 1000 * (1 + 0.6 * 255) = 1.54e8 rays
+    srv.active = [long_r, _fake_req(64, 64, 4, 14.0)]
+    assert srv._build_wave(now=14.0)[0].req is not long_r      # waited 14 s < 1.54 s / 0.1
+    long_r.rows_issued = 0
+    srv.active = [long_r, _fake_req(64, 64, 4, 16.0)]
+    assert srv._build_wave(now=16.0)[0].req is long_r          # waited 16 s > 15.4 s
+    srv.wave_rays = 1e12
+    srv.active = [_fake_req(64, 64, 4, 0.0), _fake_req(64, 64, 4, 0.0)]
+    assert len(srv._build_wave(now=0.0)) == 2                   # budgets permitting, all of them
