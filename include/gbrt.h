@@ -22,9 +22,11 @@
  *    must stay alive until the stream reaches the work.
  *  - Scenes and grids are owned by the library until gbrt_scene_free /
  *    gbrt_grid_free. A context is used by one host thread at a time.
- *  - Kernel-side failures (a grid walk that exceeds its step bound, a work
- *    queue wait that runs out) set a device error word; gbrt_sync() reports
- *    it (GBRT_ETRAVERSAL / GBRT_ETIMEDOUT) and clears it.
+ *  - Kernel-side failures (a grid walk that exceeds its step bound, a
+ *    device-side grid rebuild that outgrows its buffer) set a device error
+ *    word; gbrt_sync() reports it (GBRT_ETRAVERSAL / GBRT_ECAPACITY) and
+ *    clears it. No kernel waits on another: every work queue is a counter
+ *    that only grows, so every kernel ends.
  */
 #ifndef GBRT_H
 #define GBRT_H
@@ -51,7 +53,7 @@ extern "C" {
 #define GBRT_EINVAL (-1)      /* invalid argument or scene data */
 #define GBRT_ENOMEM (-2)      /* device or pinned allocation failed */
 #define GBRT_EDEVICE (-3)     /* CUDA runtime error / no device */
-#define GBRT_ETIMEDOUT (-4)   /* a bounded device wait ran out */
+#define GBRT_ETIMEDOUT (-4)   /* reserved: a bounded device wait ran out (no kernel of this version waits) */
 #define GBRT_ETRAVERSAL (-5)  /* a grid walk exceeded its step bound */
 #define GBRT_ECAPACITY (-6)   /* a device-side grid rebuild outgrew its buffer */
 

@@ -13,7 +13,7 @@ namespace gbrt {
 enum : uint32_t {
     ERR_DDA_STEPS = 1u,      // a grid walk exceeded nx + ny + nz + 3 steps
     ERR_SCENE_DATA = 2u,     // non-finite / non-positive scene values (device upload path)
-    ERR_QUEUE_TIMEOUT = 4u,  // a bounded wait on the work queue ran out
+    ERR_QUEUE_TIMEOUT = 4u,  // reserved: a bounded wait ran out (no kernel of this version waits)
     ERR_GRID_CAPACITY = 8u,  // a device-side grid rebuild outgrew its item buffer
 };
 
