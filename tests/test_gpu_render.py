@@ -1,4 +1,5 @@
 """GPU parity tests: the CUDA path through the C ABI against the FP64 oracle."""
+import dataclasses
 import math
 
 import numpy as np
@@ -74,6 +75,31 @@ def test_small_globule_full_frame(G, R, oracle, prec):
     assert_parity(st, "small")
     if prec == S.PRECISION_FP64:
         assert st["vis_eq"] >= 0.9999
+    R.free(scene, grid)
+
+
+@pytest.mark.parametrize("shift", [(300.0, -200.0, 500.0), (-2000.0, 1500.0, 800.0)])
+@pytest.mark.parametrize("prec", [S.PRECISION_FP64, S.PRECISION_FP32])
+def test_scene_far_from_the_origin(G, R, oracle, prec, shift):
+    # the small globule moved hundreds to thousands of units off the origin
+    # (molecular coordinates are often hundreds of angstroms): the float
+    # scene records and the FP32 walk lose absolute precision there, the
+    # parity rule must still hold against the oracle's brute force
+    w = S.small_fp64()
+    off = np.array(shift, np.float32)
+    sp = w.scene.spheres.copy()
+    sp[:, :3] += off
+    cy = w.scene.cylinders.copy()
+    cy[:, :3] += off
+    cy[:, 3:6] += off
+    sc = dataclasses.replace(w.scene, spheres=sp, cylinders=cy)
+    cam = S.ortho_camera(sc, w.width, w.height, angle_deg=25.0)
+    p = S.Params(ao_samples=8, seed=0, precision=prec)
+    scene, grid = R.upload(sc, lam=2.0)
+    rgb, ids, vis = gpu_frame(G, R, scene, grid, cam, w.width, w.height, w.lights, p)
+    ref = oracle.render(sc, cam, w.width, w.height, w.lights, p, mode="brute")
+    st = compare(rgb, ids, vis, ref)
+    assert_parity(st, f"globule moved by {shift}")
     R.free(scene, grid)
 
 
