@@ -116,6 +116,26 @@ def test_ragged_frames(G, R, oracle, W, H, spp, prec):
     R.free(scene, grid)
 
 
+@pytest.mark.parametrize("spp,shadows", [(1, False), (255, False), (1000, False), (4096, True)])
+def test_sample_counts_up_to_the_bound(G, R, oracle, spp, shadows):
+    # up to GBRT_MAX_SAMPLES AO samples a pixel (with shadows, a hit's job list
+    # is its samples plus one ray per light it faces): every job maps back to
+    # its hit and sample, so the AO counts equal the oracle's
+    w = S.small_fp64()
+    W, H = 24, 20
+    cam = S.ortho_camera(w.scene, W, H, angle_deg=10.0)
+    p = S.Params(ao_samples=spp, seed=5, precision=S.PRECISION_FP32, shadows=shadows)
+    scene, grid = R.upload(w.scene, lam=2.0)
+    rgb, ids, vis = gpu_frame(G, R, scene, grid, cam, W, H, w.lights, p)
+    ref = oracle.render(w.scene, cam, W, H, w.lights, p, mode="grid", lam=2.0)
+    st = compare(rgb, ids, vis, ref)
+    assert_parity(st, f"{spp} samples")
+    hit = ref["id"] != oracle.MISS
+    assert int(vis.max()) <= spp and int(vis[hit].max()) > 0
+    assert st["vis_eq"] >= 0.99
+    R.free(scene, grid)
+
+
 @pytest.mark.parametrize("W,H", [(65536, 1), (1, 65536)])
 def test_largest_width_and_height(G, R, oracle, W, H):
     # the largest accepted width / height: one line of pixels across the scene
