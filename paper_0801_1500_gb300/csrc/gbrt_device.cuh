@@ -149,6 +149,46 @@ __device__ __forceinline__ bool hit_object(const SceneDev& s, uint32_t id, V3<R>
     return hit_object<R>(Obj<R>::base(s), id, o, d, tmin, tmax, t);
 }
 
+// Whether the same primitive has a root in (0, tmax], without the root itself
+// (shadow and AO rays). The FP64 path multiplies the root conditions through
+// by A = |d_p|^2 > 0: the roots are t = (-B -/+ sqrt(D)) / A with B = w_p.d_p
+// and D = B^2 - A (|w_p|^2 - r^2) (= A times hit_prim's disc), so A t and
+// A s = A (w.a) + (A t)(d.a) are tested against (0, A tmax] and [0, A L],
+// which leaves one square root and no division (FP64 division and square
+// root are instruction sequences on the FP64 pipe). The FP32 path keeps
+// hit_prim, whose reciprocal and square root are single instructions.
+template <class R>
+__device__ __forceinline__ bool any_hit_prim(V3<R> o, V3<R> d, V3<R> p0, V3<R> a, R L, R r, R tmax) {
+    R t;
+    return hit_prim(o, d, p0, a, L, r, R(0), tmax, t);
+}
+
+template <>
+__device__ __forceinline__ bool any_hit_prim<double>(V3<double> o, V3<double> d, V3<double> p0, V3<double> a,
+                                                     double L, double r, double tmax) {
+    const V3<double> w = o - p0;
+    const double wa = dot(w, a), da = dot(d, a);
+    const V3<double> wp = madd(w, -wa, a), dp = madd(d, -da, a);
+    const double A = dot(dp, dp), B = dot(wp, dp);
+    const double D = fma(B, B, -A * fma(-r, r, dot(wp, wp)));
+    const double sq = sqrt(fmax(D, 0.0));
+    const double n0 = -B - sq, n1 = -B + sq;  // A t at the two roots
+    const double tA = tmax * A, LA = L * A, waA = wa * A;
+    const double s0 = fma(n0, da, waA), s1 = fma(n1, da, waA);  // A s at the two roots
+    const bool ok = D >= 0.0 && A > Num<double>::parallel_eps();
+    const bool h0 = n0 > 0.0 && n0 <= tA && s0 >= 0.0 && s0 <= LA;
+    const bool h1 = n1 > 0.0 && n1 <= tA && s1 >= 0.0 && s1 <= LA;
+    return ok && (h0 || h1);
+}
+
+template <class R>
+__device__ __forceinline__ bool any_hit_object(ObjPtr<R> obj, uint32_t id, V3<R> o, V3<R> d, R tmax) {
+    V3<R> p0, a;
+    R L, r;
+    Obj<R>::load(obj, id, p0, a, L, r);
+    return any_hit_prim<R>(o, d, p0, a, L, r, tmax);
+}
+
 // ---------------------------------------------------------------- grid walk
 
 template <class R>
@@ -372,8 +412,7 @@ __device__ bool trace_any(const GridDev& g, const SceneDev& s, V3<R> o, V3<R> d,
         uint2 cr = __ldg(g.cells + w.cell);
         for (uint32_t k = cr.x, e = cr.x + cr.y; k < e; ++k) {
             uint32_t id = __ldg(g.items + k);
-            R t;
-            if (hit_object(s, id, o, d, R(0), tmax, t)) return true;
+            if (any_hit_object<R>(Obj<R>::base(s), id, o, d, tmax)) return true;
         }
     } while (walk_next(w, overflow));
     return false;

@@ -663,8 +663,7 @@ __device__ __forceinline__ unsigned ao_test_batch(AoWarp<R, UNI>& S, int lane, u
     const unsigned r = e.x;
     const uint32_t id = e.y;
     const AoRay<R> ray = S.ray[r];
-    R t;
-    const bool hit = hit_object<R>(ao_obj(S, r, uobj), id, ray.o, ray.d, R(0), ray.tmax, t) && (unsigned)lane < n;
+    const bool hit = any_hit_object<R>(ao_obj(S, r, uobj), id, ray.o, ray.d, ray.tmax) && (unsigned)lane < n;
     return __reduce_or_sync(FULL, hit ? (1u << r) : 0u);
 }
 
