@@ -56,6 +56,7 @@ extern "C" {
 #define GBRT_ETIMEDOUT (-4)   /* reserved: a bounded device wait ran out (no kernel of this version waits) */
 #define GBRT_ETRAVERSAL (-5)  /* a grid walk exceeded its step bound */
 #define GBRT_ECAPACITY (-6)   /* a device-side grid rebuild outgrew its buffer */
+#define GBRT_EBOUNDS (-7)     /* an index outside its buffer (reported by the checked build only) */
 
 /* ---- flags ---- */
 #define GBRT_DEVICE_PTRS 0

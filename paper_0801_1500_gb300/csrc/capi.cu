@@ -213,6 +213,9 @@ int read_error_word(Ctx* c) {
         cudaMemsetAsync(c->d_err, 0, sizeof(uint32_t), c->stream);
         cudaStreamSynchronize(c->stream);
     }
+#ifdef GBRT_CHECKED
+    if (checked_violations_render() != 0) return GBRT_EBOUNDS;
+#endif
     if (w & ERR_QUEUE_TIMEOUT) return GBRT_ETIMEDOUT;
     if (w & ERR_DDA_STEPS) return GBRT_ETRAVERSAL;
     if (w & ERR_GRID_CAPACITY) return GBRT_ECAPACITY;
@@ -242,6 +245,7 @@ GBRT_API const char* gbrt_strerror(int code) {
         case GBRT_ENOMEM: return "out of device or pinned memory";
         case GBRT_EDEVICE: return "CUDA device or runtime error";
         case GBRT_ETIMEDOUT: return "a bounded device wait ran out";
+        case GBRT_EBOUNDS: return "an index fell outside its buffer (checked build)";
         case GBRT_ETRAVERSAL: return "a grid walk exceeded its step bound";
         case GBRT_ECAPACITY: return "a device-side grid rebuild outgrew its buffer";
         default: return "unknown error";

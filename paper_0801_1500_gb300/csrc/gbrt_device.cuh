@@ -12,6 +12,26 @@
 
 namespace gbrt {
 
+// ---------------------------------------------------------------- checked build
+
+// GBRT_INDEX(i, n): an index that comes from data (a cell, an item, an object
+// id, a hit slot, a pixel) into a buffer of n elements. In the normal build it
+// is i itself. In the checked build (-DGBRT_CHECKED, libgbrt_checked.so) an
+// index outside [0, n) is counted in this translation unit's g_oob and
+// replaced by 0, so the access stays inside the buffer; gbrt_sync then
+// reports GBRT_EBOUNDS.
+#ifdef GBRT_CHECKED
+static __device__ unsigned long long g_oob;
+__device__ __forceinline__ unsigned long long checked_index(unsigned long long i, unsigned long long n) {
+    if (i < n) return i;
+    atomicAdd(&g_oob, 1ull);
+    return 0ull;
+}
+#define GBRT_INDEX(i, n) ((decltype(i))::gbrt::checked_index((unsigned long long)(i), (unsigned long long)(n)))
+#else
+#define GBRT_INDEX(i, n) (i)
+#endif
+
 // ---------------------------------------------------------------- scalars
 
 template <class R>
@@ -392,9 +412,9 @@ __device__ bool trace_nearest(const GridDev& g, const SceneDev& s, V3<R> o, V3<R
     Walk<R> w;
     if (!walk_start(g, o, d, tmin, tmax, w)) return false;
     do {
-        uint2 cr = __ldg(g.cells + w.cell);
+        uint2 cr = __ldg(g.cells + GBRT_INDEX(w.cell, g.ncells));
         for (uint32_t k = cr.x, e = cr.x + cr.y; k < e; ++k) {
-            uint32_t id = __ldg(g.items + k);
+            uint32_t id = GBRT_INDEX(__ldg(g.items + GBRT_INDEX(k, g.nitems)), s.S + s.C);
             R t;
             if (hit_object(s, id, o, d, tmin, tmax, t)) nearest_consider(h, id, t);
         }
@@ -409,9 +429,9 @@ __device__ bool trace_any(const GridDev& g, const SceneDev& s, V3<R> o, V3<R> d,
     Walk<R> w;
     if (!walk_start(g, o, d, R(0), tmax, w)) return false;
     do {
-        uint2 cr = __ldg(g.cells + w.cell);
+        uint2 cr = __ldg(g.cells + GBRT_INDEX(w.cell, g.ncells));
         for (uint32_t k = cr.x, e = cr.x + cr.y; k < e; ++k) {
-            uint32_t id = __ldg(g.items + k);
+            uint32_t id = GBRT_INDEX(__ldg(g.items + GBRT_INDEX(k, g.nitems)), s.S + s.C);
             if (any_hit_object<R>(Obj<R>::base(s), id, o, d, tmax)) return true;
         }
     } while (walk_next(w, overflow));

@@ -172,6 +172,12 @@ int render_frames(Ctx* ctx, FrameDev* frames, int n, bool use_graph);
 // the four wavefront kernels with grids sized for the current device.
 int configure_render_kernels();
 int enqueue_prepared(const BatchDev& bd, int precision, cudaStream_t stream, int block, int num_sms, bool patch);
+
+#ifdef GBRT_CHECKED
+// checked build: indices the render kernels found outside their buffers since
+// the last call (cleared as read)
+unsigned long long checked_violations_render();
+#endif
 int launch_ao_probe(Ctx* ctx, const FrameDev& f, const double* pts, const double* nrm, int64_t n, float* out);
 int launch_philox(Ctx* ctx, const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out);
 

@@ -46,6 +46,7 @@ struct GridDev {
     int32_t n[3];
     int32_t empty;
     int64_t ncells;
+    int64_t nitems;  // length of the item buffer
     const uint2* cells;
     const uint32_t* items;
 };
@@ -131,6 +132,7 @@ struct BatchDev {
     unsigned int* lmask;
     unsigned long long* queue;
     unsigned int* err;
+    int64_t hit_cap;  // hit slots (records, vis, lmask) of the batch
     int32_t nframes;
     int32_t tile_w, tile_h;
     int32_t refill;

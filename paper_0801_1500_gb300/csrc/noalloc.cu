@@ -119,6 +119,7 @@ extern "C" GBRT_API int gbrt_render_noalloc(const gbrt_scene* scene, const gbrt_
         bd.hits = base + OFF_HITS;
         bd.vis = (unsigned int*)(base + OFF_VIS);
         bd.lmask = (unsigned int*)(base + OFF_LMASK);
+        bd.hit_cap = (int64_t)width * height;
         bd.nframes = 1;
         bd.tile_w = tw;
         bd.tile_h = th;

@@ -415,7 +415,7 @@ __global__ void __launch_bounds__(256) k_primary(const __grid_constant__ BatchDe
         if (!inside) continue;
         const uint32_t q = (uint32_t)j * (uint32_t)F.W + (uint32_t)i;
         if (hit) {
-            const int64_t slot = F.hit_base + base + __popc(hm & ((1u << lane) - 1u));
+            const int64_t slot = GBRT_INDEX(F.hit_base + base + __popc(hm & ((1u << lane) - 1u)), b.hit_cap);
             if (MODE == GBRT_FP32) {
                 // the refined offset w from p0 splits into its foot on the
                 // generator (centre or axis), p0 + (w.a) a, and w_p, the
@@ -512,7 +512,7 @@ __device__ __forceinline__ bool ao_job(const BatchDev& b, unsigned long long jj,
         h = (uint32_t)jl;
     }
     const uint32_t smp = (uint32_t)(jl - (unsigned long long)h * jph);
-    J.vslot = F.hit_base + h;
+    J.vslot = GBRT_INDEX(F.hit_base + (int64_t)h, b.hit_cap);
     V3<R> n;
     uint32_t q;
     HitIO<R>::load(b.hits, J.vslot, J.o, n, q, J.self);
@@ -618,6 +618,10 @@ template <class R, bool UNI>
 struct AoPtrs {
     ObjPtr<R> obj[32];
     const uint32_t* items[32];
+#ifdef GBRT_CHECKED
+    int64_t nitems[32];  // the lengths the checked build tests indices against
+    int64_t nobj[32];
+#endif
 };
 template <class R>
 struct AoPtrs<R, true> {};
@@ -652,6 +656,24 @@ __device__ __forceinline__ const uint32_t* ao_items(const AoWarp<R, UNI>& S, uns
     if constexpr (UNI) return uni;
     else return S.items[r];
 }
+#ifdef GBRT_CHECKED
+// ray r's item-buffer length and object count (the checked build's bounds)
+template <class R, bool UNI>
+__device__ __forceinline__ int64_t ao_nitems(const AoWarp<R, UNI>& S, unsigned r, int64_t uni) {
+    if constexpr (UNI) return uni;
+    else return S.nitems[r];
+}
+template <class R, bool UNI>
+__device__ __forceinline__ int64_t ao_nobj(const AoWarp<R, UNI>& S, unsigned r, int64_t uni) {
+    if constexpr (UNI) return uni;
+    else return S.nobj[r];
+}
+#define GBRT_AO_ITEM(idx, r) GBRT_INDEX(idx, ao_nitems(S, r, unitems))
+#define GBRT_AO_OBJ(id, r) GBRT_INDEX(id, ao_nobj(S, r, unobj))
+#else
+#define GBRT_AO_ITEM(idx, r) (idx)
+#define GBRT_AO_OBJ(id, r) (id)
+#endif
 
 // FP64 path: test queued pairs [0, n) (1 <= n <= 32), one per lane (lanes
 // past n redo pair 0 and discard it, so the batch runs without branches);
@@ -685,6 +707,10 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
         uitems = b.frames[0].grid.items;
         ucells = b.frames[0].grid.cells;
     }
+#ifdef GBRT_CHECKED
+    const int64_t unitems = b.frames[0].grid.nitems;
+    const int64_t unobj = (int64_t)b.frames[0].scene.S + b.frames[0].scene.C;
+#endif
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     const unsigned long long total = b.job_off[b.nframes];
@@ -730,6 +756,10 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
                             cells = J.F->grid.cells;
                             S.obj[lane] = Obj<R>::base(J.F->scene);
                             S.items[lane] = J.F->grid.items;
+#ifdef GBRT_CHECKED
+                            S.nitems[lane] = J.F->grid.nitems;
+                            S.nobj[lane] = (int64_t)J.F->scene.S + J.F->scene.C;
+#endif
                         }
                         AoRay<R> ray;
                         ray.o = J.o;
@@ -747,7 +777,7 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
                         }
                         // the walk stands on its first cell: its record waits in
                         // the fifo, so every later cell comes from a step
-                        S.fifo[lane][0] = __ldg(cells + w.cell);
+                        S.fifo[lane][0] = __ldg(cells + GBRT_INDEX(w.cell, w.ncells));
                         nf = 1;
                         wend = false;
                         has = true;
@@ -788,7 +818,7 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
             const bool queued = has && g < AO_CELLS - 1 && (unsigned)g < nf;
             if (queued) cr = S.fifo[lane][g];
             if (has && !queued && !wend) {
-                if (walk_step(w)) cr = __ldg(cells + w.cell);
+                if (walk_step(w)) cr = __ldg(cells + GBRT_INDEX(w.cell, w.ncells));
                 else wend = true;
             }
             if (has && (queued || !wend)) avail = (unsigned)g + 1u;
@@ -850,7 +880,7 @@ __global__ void __launch_bounds__(256) k_ao_walk(const __grid_constant__ BatchDe
                 di = p >= st.y ? so.y : di;
                 di = p >= st.z ? so.z : di;
                 di = p >= st.w ? so.w : di;
-                const uint32_t id = __ldg(ao_items(S, r, uitems) + (p + di));
+                const uint32_t id = GBRT_AO_OBJ(__ldg(ao_items(S, r, uitems) + GBRT_AO_ITEM(p + di, r)), r);
                 if constexpr (AoCfg<R>::queue) {
                     uint32_t* slot = &S.mbox[r][id & (AoCfg<R>::mbox - 1)];
                     const bool keep = base + lane < T && *slot != id;
@@ -903,11 +933,12 @@ __global__ void __launch_bounds__(256) k_shade(const __grid_constant__ BatchDev 
          g += (unsigned long long)gridDim.x * blockDim.x) {
         const int f = find_frame(b.hit_off, b.nframes, g);
         const FrameDev& F = b.frames[f];
-        const int64_t slot = F.hit_base + (int64_t)(g - b.hit_off[f]);
+        const int64_t slot = GBRT_INDEX(F.hit_base + (int64_t)(g - b.hit_off[f]), b.hit_cap);
         V3<R> o, n;
         uint32_t q, id;
         HitIO<R>::load(b.hits, slot, o, n, q, id);
-        q &= ~HIT_INSIDE;
+        q = GBRT_INDEX(q & ~HIT_INSIDE, (uint32_t)F.W * (uint32_t)F.H);
+        id = GBRT_INDEX(id, F.scene.S + F.scene.C);
         const uint32_t vis = b.vis[slot];
         V3<R> d;
         if (std::is_same<R, float>::value) {
@@ -922,7 +953,11 @@ __global__ void __launch_bounds__(256) k_shade(const __grid_constant__ BatchDev 
         const uint32_t lit = F.shadows ? b.lmask[slot] : 0xFFFFFFFFu;
         R rgb[3];
         shade<R>(F, id, n, d, V, lit, rgb);
-        R* out = (R*)F.out_rgb + 3 * (size_t)(q - F.rgb_q0);
+        // the colour buffer holds pixels [rgb_q0, ...): the whole image (rgb_q0 = 0)
+        // or, for a supersampled frame, the finer raster's band (rgb_q0 = row0 W);
+        // either way the band's pixels end at (row0 + rows) W
+        R* out = (R*)F.out_rgb +
+                 3 * (size_t)GBRT_INDEX((int64_t)q - F.rgb_q0, (int64_t)(F.row0 + F.rows) * F.W - F.rgb_q0);
         out[0] = rgb[0];
         out[1] = rgb[1];
         out[2] = rgb[2];
@@ -1277,6 +1312,7 @@ int render_frames(Ctx* ctx, FrameDev* frames, int n, bool use_graph) {
     bd.vis = ctx->d_vis;
     bd.lmask = ctx->d_lmask;
     bd.err = ctx->d_err;
+    bd.hit_cap = (int64_t)px;
     bd.nframes = n;
     bd.tile_w = tw;
     bd.tile_h = th;
@@ -1368,5 +1404,16 @@ int launch_philox(Ctx* ctx, const uint32_t* ctr, const uint32_t* key, int64_t n,
     ctx->launches++;
     return cudaGetLastError() == cudaSuccess ? GBRT_OK : GBRT_EDEVICE;
 }
+
+#ifdef GBRT_CHECKED
+// Indices the checked build found outside their buffers since the last call
+// (the render kernels' counter), cleared as it is read.
+unsigned long long checked_violations_render() {
+    unsigned long long v = 0, z = 0;
+    if (cudaMemcpyFromSymbol(&v, g_oob, sizeof(v)) != cudaSuccess) return 0;
+    cudaMemcpyToSymbol(g_oob, &z, sizeof(z));
+    return v;
+}
+#endif
 
 }  // namespace gbrt

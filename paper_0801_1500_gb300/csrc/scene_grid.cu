@@ -592,7 +592,7 @@ __device__ __forceinline__ float float_of_ord_dev(uint32_t o) {
 
 // Device-side rebuild, step 1 (one thread): geometry from the current scene box.
 __global__ void k_grid_geometry(const uint32_t* box, int64_t N, float lambda, int64_t cells_cap, const uint2* cells,
-                                const uint32_t* items, GridDev* geom, BuildAux* aux) {
+                                const uint32_t* items, int64_t items_cap, GridDev* geom, BuildAux* aux) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     float lo[3], hi[3];
     for (int k = 0; k < 3; ++k) {
@@ -604,6 +604,7 @@ __global__ void k_grid_geometry(const uint32_t* box, int64_t N, float lambda, in
     grid_geometry(lo, hi, N, lambda, cells_cap, d, a);
     d.cells = cells;
     d.items = items;
+    d.nitems = items_cap;
     *geom = d;
     *aux = a;
 }
@@ -696,6 +697,7 @@ int grid_build(Ctx* ctx, const Scene* s, float lambda, Grid* g) {
         GB_TRY(cudaStreamSynchronize(ctx->stream));
         d.cells = g->cells;
         d.items = g->items;
+        d.nitems = std::max<int64_t>(g->refs, 1);
         g->bytes = (size_t)nc * sizeof(uint2) + (size_t)std::max<int64_t>(g->refs, 1) * sizeof(uint32_t);
     }
     cudaFree(counts);
@@ -796,6 +798,7 @@ static int dyn_alloc(Grid* g, int64_t cells_cap, int64_t items_cap) {
     g->bytes = (size_t)cells_cap * (sizeof(uint2) + sizeof(uint32_t)) + (size_t)items_cap * sizeof(uint32_t);
     g->dev.cells = g->cells;
     g->dev.items = g->items;
+    g->dev.nitems = items_cap;
     return GBRT_OK;
 }
 
@@ -846,7 +849,8 @@ int grid_rebuild(Ctx* ctx, const Scene* s, Grid* g) {
     const int64_t nb = (nc + SCAN_TILE - 1) / SCAN_TILE;
     const int blocksN = (int)((std::max<int64_t>(N, 1) + 255) / 256);
     if (cudaMemsetAsync(g->d_counts, 0, (size_t)nc * sizeof(uint32_t), st) != cudaSuccess) return GBRT_EDEVICE;
-    k_grid_geometry<<<1, 32, 0, st>>>(s->d_box, N, g->lambda, nc, g->cells, g->items, g->d_geom, g->d_aux);
+    k_grid_geometry<<<1, 32, 0, st>>>(s->d_box, N, g->lambda, nc, g->cells, g->items, g->items_cap, g->d_geom,
+                                      g->d_aux);
     if (N > 0) {
         k_grid_count<<<object_warp_blocks(N), 256, 0, st>>>(s->aabb, s->obj, N, &g->d_aux->p, g->d_counts, g->d_reach);
         k_bound_radius<<<blocksN, 256, 0, st>>>(s->obj64, N, g->d_aux->ctr, &g->d_aux->rbits);

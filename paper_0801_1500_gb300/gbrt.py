@@ -15,9 +15,11 @@ import numpy as np
 
 from . import build as _build
 
-LIB_PATH = _build.LIB
+# GBRT_LIB_VARIANT=checked loads the checked build (indices tested against
+# their buffers; see build.py)
+LIB_PATH = _build.LIB_CHECKED if os.environ.get("GBRT_LIB_VARIANT") == "checked" else _build.LIB
 
-OK, EINVAL, ENOMEM, EDEVICE, ETIMEDOUT, ETRAVERSAL, ECAPACITY = 0, -1, -2, -3, -4, -5, -6
+OK, EINVAL, ENOMEM, EDEVICE, ETIMEDOUT, ETRAVERSAL, ECAPACITY, EBOUNDS = 0, -1, -2, -3, -4, -5, -6, -7
 DEVICE_PTRS, HOST_PTRS, BATCH_GRAPH, HOST_ASYNC = 0, 1, 2, 4
 FP32, FP64 = 0, 1
 CAMERA_ORTHO, CAMERA_PINHOLE = 0, 1

@@ -31,15 +31,21 @@ def test_every_declared_symbol_is_exported(G):
     assert len(names) >= 19
     for n in names:
         assert hasattr(G.lib, n), n
-    out = subprocess.run(["nm", "-D", "--defined-only", G.LIB_PATH], capture_output=True, text=True).stdout
-    exported = set(re.findall(r"\bT (gbrt_\w+)", out))
-    assert set(names) == exported
+    from paper_0801_1500_gb300 import build
+    for lib in (G.LIB_PATH, build.LIB, build.LIB_CHECKED):   # the checked build exports the same ABI
+        out = subprocess.run(["nm", "-D", "--defined-only", lib], capture_output=True, text=True).stdout
+        exported = set(re.findall(r"\bT (gbrt_\w+)", out))
+        assert set(names) == exported, lib
 
 
 def test_version_and_errors(G):
     text = open(HEADER).read()
     assert G.gbrt_version() == int(re.search(r"#define GBRT_VERSION (\d+)", text).group(1))
-    for code in (G.OK, G.EINVAL, G.ENOMEM, G.EDEVICE, G.ETIMEDOUT, G.ETRAVERSAL):
+    codes = {k: int(v) for k, v in re.findall(r"#define GBRT_(E\w+|OK) \(?(-?\d+)\)?", text)}
+    assert codes == {"OK": G.OK, "EINVAL": G.EINVAL, "ENOMEM": G.ENOMEM, "EDEVICE": G.EDEVICE,
+                     "ETIMEDOUT": G.ETIMEDOUT, "ETRAVERSAL": G.ETRAVERSAL, "ECAPACITY": G.ECAPACITY,
+                     "EBOUNDS": G.EBOUNDS}
+    for code in codes.values():
         assert G.strerror(code) and G.strerror(code) != "unknown error"
     assert G.strerror(-99) == "unknown error"
     assert G.PROFILE_ALL == int(re.search(r"#define GBRT_PROFILE_ALL (\d+)", text).group(1))
