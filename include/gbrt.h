@@ -26,7 +26,9 @@
  *    device-side grid rebuild that outgrows its buffer) set a device error
  *    word; gbrt_sync() reports it (GBRT_ETRAVERSAL / GBRT_ECAPACITY) and
  *    clears it. No kernel waits on another: every work queue is a counter
- *    that only grows, so every kernel ends.
+ *    that only grows, so every kernel ends. The checked build of the
+ *    library (libgbrt_checked.so) also tests every index that comes from
+ *    data against its buffer and reports a stray one as GBRT_EBOUNDS.
  */
 #ifndef GBRT_H
 #define GBRT_H
