@@ -112,6 +112,29 @@ def test_dda_visits_every_cell_on_the_path(oracle, lam):
             assert np.all(steps == 1)
 
 
+@pytest.mark.parametrize("lam", [125.0, 1000.0, 8000.0])
+@pytest.mark.parametrize("yz", [(4.0, 0.3), (3.0, -3.0)])
+def test_walk_counts_cells_up_to_the_hit_cell(oracle, lam, yz):
+    # One sphere (radius 5 at the origin) listed in every cell of its box; a
+    # ray along +x at offset (y, z) meets it at x = -sqrt(25 - y^2 - z^2). The
+    # nearest-hit walk must count every cell from the box face to the cell
+    # holding that point -- earlier cells list the sphere too, and testing it
+    # there already finds the hit, but a nearer hit could still lie in a later
+    # cell before it -- and none after: floor((x_hit - lo) / h) + 1 cells, one
+    # sphere test in each.
+    sc = S.make_scene([[0.0, 0.0, 0.0, 5.0]])
+    gi = oracle.grid_info(sc, lam=lam)
+    y, z = yz
+    x_hit = -math.sqrt(25.0 - y * y - z * z)
+    h = (gi["hi"][0] - gi["lo"][0]) / gi["dims"][0]
+    expect = math.floor((x_hit - gi["lo"][0]) / h) + 1
+    assert expect >= 2
+    d = oracle.nearest_detail(sc, np.array([[-20.0, y, z]]), np.array([[1.0, 0.0, 0.0]]), mode="grid", lam=lam)
+    assert d["id"][0] == 0 and d["t"][0] == pytest.approx(20.0 + x_hit, abs=1e-12)
+    cells, sphere_tests, cylinder_tests = (int(c) for c in d["counters"])
+    assert (cells, sphere_tests, cylinder_tests) == (expect, expect, 0)
+
+
 def test_grid_reference_count(oracle):
     # every object is listed in exactly the cells its padded box overlaps
     sc = tiny_scene(4, n_sph=30, n_cyl=0)
