@@ -34,6 +34,7 @@ def lib():
         L.oracle_hit_sphere.argtypes = [P, P, P, f64, f64, f64, P, P]
         L.oracle_hit_cylinder.argtypes = [P, P, P, P, f64, f64, f64, P, P]
         L.oracle_nearest.argtypes = [i64, P, i64, P, i32, f64, i64, P, P, f64, f64, P, P, P, P, P, P]
+        L.oracle_anyhit.argtypes = [i64, P, i64, P, i32, f64, i64, P, P, f64, P, P]
         L.oracle_grid_walk.argtypes = [i64, P, i64, P, f64, P, P, f64, f64, i64, P, P]
         L.oracle_grid_info.argtypes = [i64, P, i64, P, f64, P, P, P]
         L.oracle_ao_probe.argtypes = [i64, P, i64, P, i32, f64, i64, P, P, i32, u64, u32, f64, f64, P, i32]
@@ -148,6 +149,23 @@ def nearest_detail(scene, orig, dirs, mode="brute", lam=1.0, tmin=0.0, tmax=math
     if rc:
         raise RuntimeError("oracle_nearest failed")
     return dict(id=ids, t=ts, grazing=gz.astype(bool), id2=id2, idg=idg, counters=cnt)
+
+
+def anyhit(scene, orig, dirs, mode="brute", lam=1.0, tmax=math.inf):
+    """Any hit in (0, tmax] of explicit rays (directions are normalised), as
+    (hit bool per ray, counters: cells, sphere tests, cylinder tests)."""
+    sph, cyl, _, _ = _scene_arrays(scene)
+    o = _f64(orig, (-1, 3))
+    d = _f64(dirs, (-1, 3))
+    d = np.ascontiguousarray(d / np.linalg.norm(d, axis=1, keepdims=True))
+    n = o.shape[0]
+    hit = np.zeros(n, np.uint8)
+    cnt = np.zeros(3, np.int64)
+    rc = lib().oracle_anyhit(sph.shape[0], _p(sph), cyl.shape[0], _p(cyl), MODES[mode], float(lam), n, _p(o), _p(d),
+                             float(tmax), _p(hit), _p(cnt))
+    if rc:
+        raise RuntimeError("oracle_anyhit failed")
+    return hit.astype(bool), cnt
 
 
 def nearest(scene, orig, dirs, mode="brute", lam=1.0, tmin=0.0, tmax=math.inf):

@@ -768,6 +768,27 @@ int oracle_nearest(int64_t S, const double* sph, int64_t C, const double* cyl, i
     return 0;
 }
 
+/* Any hit in (0, tmax] of explicit rays (o, d unit), the query of an AO or
+ * shadow ray: out_hit[r] = 1 when ray r meets an object; counters = cells
+ * walked, sphere tests and cylinder tests over all rays (the AO rays' work
+ * counts of the roofline come from this walk). */
+int oracle_anyhit(int64_t S, const double* sph, int64_t C, const double* cyl, int32_t mode, double lambda,
+                  int64_t nrays, const double* orig, const double* dirs, double tmax, uint8_t* out_hit,
+                  int64_t* counters)
+{
+    oworld w;
+    if (world_init(&w, S, sph, C, cyl, NULL, NULL, 0, mode, lambda)) return -1;
+    ocount tot = {0, 0, 0};
+    for (int64_t r = 0; r < nrays; ++r) {
+        ocount cnt = {0, 0, 0};
+        out_hit[r] = (uint8_t)world_anyhit(&w, orig + 3 * r, dirs + 3 * r, tmax, &cnt);
+        tot.cells += cnt.cells; tot.sph += cnt.sph; tot.cyl += cnt.cyl;
+    }
+    if (counters) { counters[0] = tot.cells; counters[1] = tot.sph; counters[2] = tot.cyl; }
+    grid_free(&w.gr);
+    return 0;
+}
+
 /* Visited cells (flattened indices) of one ray walking the whole grid. */
 int oracle_grid_walk(int64_t S, const double* sph, int64_t C, const double* cyl, double lambda,
                      const double o[3], const double d[3], double tmin, double tmax,

@@ -30,6 +30,12 @@ MUTANTS = {
     "cyl_dp": ("double tc = -dot3(wp, dp) / A;", "double tc = dot3(wp, dp) / A;"),
     "dda_tie": ("if (nr->id1 != OR_MISS && nr->t1 <= dda_cell_exit(&w)) break;",
                 "if (nr->id1 != OR_MISS) break;"),
+    "anyhit_nocount": ("        cnt->cells++;\n        int64_t c = ((int64_t)w.c[2] * gr->n[1] + w.c[1]) * gr->n[0] + w.c[0];\n"
+                       "        for (int64_t i = gr->start[c]; i < gr->start[c + 1]; ++i) {",
+                       "        int64_t c = ((int64_t)w.c[2] * gr->n[1] + w.c[1]) * gr->n[0] + w.c[0];\n"
+                       "        for (int64_t i = gr->start[c]; i < gr->start[c + 1]; ++i) {"),
+    "anyhit_kind": ("            if (id < sc->S) cnt->sph++; else cnt->cyl++;", "            cnt->sph++;"),
+    "anyhit_one_cell": ("    } while (dda_next(gr, &w));\n    return 0;", "    } while (0);\n    return 0;"),
     "grid_nopad": ("c0[k] = cell_coord(gr, k, a[k] - pad); c1[k] = cell_coord(gr, k, b[k] + pad);",
                    "c0[k] = cell_coord(gr, k, a[k] + 0.3); c1[k] = cell_coord(gr, k, b[k] - 0.3);"),
     "refine_normal": ("if (dot3(n, d) > 0.0) { n[0] = -n[0]; n[1] = -n[1]; n[2] = -n[2]; }",

@@ -135,6 +135,43 @@ def test_walk_counts_cells_up_to_the_hit_cell(oracle, lam, yz):
     assert (cells, sphere_tests, cylinder_tests) == (expect, expect, 0)
 
 
+@pytest.mark.parametrize("lam", [125.0, 1000.0, 8000.0])
+def test_anyhit_walk_counts(oracle, lam):
+    # The any-hit walk (AO and shadow rays) stops at the first test that hits.
+    # One sphere listed in every cell of its box: a ray meeting it is done in
+    # the cell where it enters the box (1 cell, 1 test); a ray through the box
+    # that misses it walks every cell along x (n_x cells, one test each). A
+    # tube along x, seen by a ray parallel to its axis inside its box, is
+    # tested in every cell and never hit.
+    sph = S.make_scene([[0.0, 0.0, 0.0, 5.0]])
+    nx = oracle.grid_info(sph, lam=lam)["dims"][0]
+    hit, cnt = oracle.anyhit(sph, np.array([[-20.0, 4.0, 0.3]]), np.array([[1.0, 0.0, 0.0]]), mode="grid", lam=lam)
+    assert hit[0] and tuple(cnt) == (1, 1, 0)
+    hit, cnt = oracle.anyhit(sph, np.array([[-20.0, 4.5, 4.5]]), np.array([[1.0, 0.0, 0.0]]), mode="grid", lam=lam)
+    assert not hit[0] and tuple(cnt) == (nx, nx, 0)
+    tube = S.make_scene(np.zeros((0, 4)), [[-5.0, 0.0, 0.0, 5.0, 0.0, 0.0, 1.0]])
+    nx = oracle.grid_info(tube, lam=lam)["dims"][0]
+    hit, cnt = oracle.anyhit(tube, np.array([[-20.0, 0.9, 0.9]]), np.array([[1.0, 0.0, 0.0]]), mode="grid", lam=lam)
+    assert not hit[0] and tuple(cnt) == (nx, 0, nx)
+
+
+@pytest.mark.parametrize("tmax", [math.inf, 3.0])
+def test_anyhit_equals_brute_force_and_nearest(oracle, tmax):
+    # grid and brute-force any-hit agree, and both say "hit" exactly when the
+    # nearest hit lies in (0, tmax]
+    sc = S.globule(200, 190, 10.0, seed=4)
+    rng = np.random.default_rng(11)
+    o = rng.uniform(-12.0, 12.0, (3000, 3))
+    d = rng.normal(size=(3000, 3))
+    hg, _ = oracle.anyhit(sc, o, d, mode="grid", lam=4.0, tmax=tmax)
+    hb, _ = oracle.anyhit(sc, o, d, mode="brute", tmax=tmax)
+    ids, ts, _, _ = oracle.nearest(sc, o, d, mode="brute")
+    near = (ids != oracle.MISS) & (ts <= tmax)
+    assert np.array_equal(hg, hb)
+    assert np.array_equal(hb, near)
+    assert 0.1 < hb.mean() < 0.9
+
+
 def test_grid_reference_count(oracle):
     # every object is listed in exactly the cells its padded box overlaps
     sc = tiny_scene(4, n_sph=30, n_cyl=0)
